@@ -1,0 +1,232 @@
+"""FP64 CPU oracle of the Instant4D rasterizer and grid pruning -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  The product (``paper_2510_01119_gb300``) never does, and this package imports
+nothing from the product: the two share no code.  The arithmetic lives in ``i4d_oracle.c``
+(plain C, float64) and ``adam.py`` (numpy float64); this file only marshals numpy arrays.
+
+Paper: Instant4D (arXiv 2510.01119).  Eq. 5 back-projection, Sec. 3.2 grid pruning, Eq. 7-8
+conditional mean/covariance, Eq. 9 and the temporal-opacity cull of Sec. 3.3, the isotropic
+variant of Sec. 3.3, and the 3D splatting renderer of Sec. 3.1 (Eq. 3) that the method builds on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from .adam import adam_step  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "i4d_oracle.c")
+_LIB = os.path.join(_HERE, "libi4d_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_FULL, MODE_ISO_ROT, MODE_ISO_IDENTITY = 0, 1, 2
+
+# projected-record columns (must follow the enum in i4d_oracle.c)
+PCOLS = ["visible", "u", "v", "depth", "ot", "ca", "cb", "cc", "radius", "r", "g", "b",
+         "x0", "y0", "x1", "y1", "margin", "rect_margin",
+         "m3x", "m3y", "m3z", "s3xx", "s3xy", "s3xz", "s3yy", "s3yz", "s3zz"]
+P = {name: k for k, name in enumerate(PCOLS)}
+# 2D-gradient columns
+GCOLS = ["u", "v", "ca", "cb", "cc", "ot", "r", "g", "b"]
+
+# Thresholds the paper leaves to the 3D splatting renderer it builds on (readings C3, C4).
+DEFAULT_SETTINGS = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, q_max=9.0,
+                        ot_min=1.0 / 255.0, z_near=0.2, dilation=0.3, fov_clamp=1.3)
+_SETTING_ORDER = ["alpha_max", "alpha_min", "T_min", "q_max", "ot_min", "z_near", "dilation", "fov_clamp"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (no CUDA); returns the shared-library path."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                                   "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.orc_tile_pairs.restype = ctypes.c_long
+        lib.orc_prune.restype = ctypes.c_long
+        _lib = lib
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def settings_array(**overrides) -> np.ndarray:
+    s = dict(DEFAULT_SETTINGS)
+    for k, v in overrides.items():
+        if k not in s:
+            raise KeyError(k)
+        s[k] = v
+    return np.array([s[k] for k in _SETTING_ORDER], dtype=np.float64)
+
+
+def camera_array(cam: dict) -> np.ndarray:
+    """cam: dict(R (3,3) world->camera, t (3,), fx, fy, cx, cy, W, H, time)."""
+    a = np.zeros(20, dtype=np.float64)
+    a[0:9] = np.asarray(cam["R"], dtype=np.float64).reshape(9)
+    a[9:12] = np.asarray(cam["t"], dtype=np.float64).reshape(3)
+    a[12], a[13], a[14], a[15] = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    a[16], a[17], a[18] = cam["W"], cam["H"], cam["time"]
+    return a
+
+
+def _gauss_arrays(g: dict):
+    n = g["mean4"].shape[0]
+    sh = g.get("sh")
+    sh_arr = np.zeros((n, 15, 3), dtype=np.float64)
+    if sh is not None and sh.size:
+        k = sh.shape[1]
+        sh_arr[:, :k, :] = sh
+    return (n, int(g.get("sh_deg", 0)), int(g.get("mode", MODE_FULL)), _f64(g["mean4"]), _f64(g["logscale4"]),
+            _f64(g["ql"]), _f64(g["qr"]), _f64(g["opacity"]), _f64(g["rgb"]), np.ascontiguousarray(sh_arr))
+
+
+def project(g: dict, cam: dict, tile=(16, 16), settings=None) -> np.ndarray:
+    """Eq. 7-8 slicing, temporal opacity, EWA projection and colour for every Gaussian -> (n, 27)."""
+    lib = _load()
+    n, deg, mode, m4, ls4, ql, qr, op, rgb, sh = _gauss_arrays(g)
+    S = settings if settings is not None else settings_array()
+    out = np.zeros((n, len(PCOLS)), dtype=np.float64)
+    rc = lib.orc_project(n, deg, mode, _ptr(m4), _ptr(ls4), _ptr(ql), _ptr(qr), _ptr(op), _ptr(rgb), _ptr(sh),
+                         _ptr(camera_array(cam)), int(tile[0]), int(tile[1]), _ptr(S), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_project failed ({rc})")
+    return out
+
+
+def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=None):
+    """Per-pixel depth-sorted compositing -> (img (npix,3), T_final, n_contrib, margin)."""
+    lib = _load()
+    n = proj.shape[0]
+    W, H = int(cam["W"]), int(cam["H"])
+    S = settings if settings is not None else settings_array()
+    pix_arr = None if pix is None else np.ascontiguousarray(pix, dtype=np.int32)
+    npix = W * H if pix is None else pix_arr.shape[0]
+    img = np.zeros((npix, 3), dtype=np.float64)
+    T = np.zeros(npix, dtype=np.float64)
+    nc = np.zeros(npix, dtype=np.int32)
+    mg = np.zeros(npix, dtype=np.float64)
+    rc = lib.orc_render(n, _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S),
+                        npix, _ptr(pix_arr), _ptr(img), _ptr(T), _ptr(nc), _ptr(mg))
+    if rc != 0:
+        raise RuntimeError(f"orc_render failed ({rc})")
+    return img, T, nc, mg
+
+
+def render_bwd(g: dict, cam: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), settings=None, pix=None):
+    """Analytic backward for one camera -> (grad2d (n,9), dict of parameter gradients)."""
+    lib = _load()
+    n, deg, mode, m4, ls4, ql, qr, op, rgb, sh = _gauss_arrays(g)
+    W, H = int(cam["W"]), int(cam["H"])
+    S = settings if settings is not None else settings_array()
+    pix_arr = None if pix is None else np.ascontiguousarray(pix, dtype=np.int32)
+    npix = W * H if pix is None else pix_arr.shape[0]
+    gimg = _f64(dL_dimg).reshape(npix, 3)
+    g2 = np.zeros((n, 9), dtype=np.float64)
+    grads = dict(mean4=np.zeros((n, 4)), logscale4=np.zeros((n, 4)), ql=np.zeros((n, 4)), qr=np.zeros((n, 4)),
+                 opacity=np.zeros(n), rgb=np.zeros((n, 3)), sh=np.zeros((n, 15, 3)))
+    rc = lib.orc_render_bwd(n, deg, mode, _ptr(m4), _ptr(ls4), _ptr(ql), _ptr(qr), _ptr(op), _ptr(rgb), _ptr(sh),
+                            _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), _ptr(gimg),
+                            _ptr(g2), _ptr(grads["mean4"]), _ptr(grads["logscale4"]), _ptr(grads["ql"]),
+                            _ptr(grads["qr"]), _ptr(grads["opacity"]), _ptr(grads["rgb"]), _ptr(grads["sh"]))
+    if rc != 0:
+        raise RuntimeError(f"orc_render_bwd failed ({rc})")
+    grads["sh"] = grads["sh"][:, : (deg + 1) ** 2 - 1, :]
+    return g2, grads
+
+
+def tile_pairs(proj: np.ndarray, cam: dict, tile=(16, 16), tile_offset: int = 0):
+    """(tile, id) pairs of the visible Gaussians' tile rectangles in (tile, depth, id) order."""
+    lib = _load()
+    tiles_x = (int(cam["W"]) + tile[0] - 1) // tile[0]
+    vis = proj[:, P["visible"]] != 0
+    area = ((proj[:, P["x1"]] - proj[:, P["x0"]]) * (proj[:, P["y1"]] - proj[:, P["y0"]]))[vis]
+    cap = int(area.sum())
+    tiles = np.zeros(max(cap, 1), dtype=np.int32)
+    ids = np.zeros(max(cap, 1), dtype=np.int32)
+    cnt = lib.orc_tile_pairs(proj.shape[0], _ptr(np.ascontiguousarray(proj)), tiles_x, int(tile_offset),
+                             ctypes.c_long(cap), _ptr(tiles), _ptr(ids))
+    if cnt < 0:
+        raise RuntimeError(f"orc_tile_pairs failed ({cnt})")
+    return tiles[:cnt], ids[:cnt]
+
+
+def backproject(cam: dict, depth: np.ndarray) -> np.ndarray:
+    """Eq. 5 for every pixel of one depth map -> (H*W, 3) float64 world points."""
+    lib = _load()
+    H, W = depth.shape
+    assert W == int(cam["W"]) and H == int(cam["H"])
+    out = np.zeros((H * W, 3), dtype=np.float64)
+    lib.orc_backproject(_ptr(camera_array(cam)), _ptr(np.ascontiguousarray(depth, dtype=np.float32)), _ptr(out))
+    return out
+
+
+def prune(xyz: np.ndarray, voxel_static: float, voxel_dynamic: float = None, min_support: int = 1,
+          rgb: np.ndarray = None, t: np.ndarray = None, dyn: np.ndarray = None):
+    """Grid pruning of a float32 point cloud (Sec. 3.2).  The voxel index of a coordinate is the
+    floor of one float32 product with the float32 reciprocal of the voxel size."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    npts = xyz.shape[0]
+    inv_s = np.float32(1.0) / np.float32(voxel_static)
+    inv_d = np.float32(1.0) / np.float32(voxel_dynamic if voxel_dynamic is not None else voxel_static)
+    cap = max(npts, 1)
+    rep = np.zeros(cap, dtype=np.uint32)
+    cnt = np.zeros(cap, dtype=np.int32)
+    cen = np.zeros((cap, 3), dtype=np.float64)
+    mrgb = np.zeros((cap, 3), dtype=np.float64)
+    mt = np.zeros(cap, dtype=np.float64)
+    flag = np.zeros(cap, dtype=np.uint8)
+    rgb_a = None if rgb is None else np.ascontiguousarray(rgb, dtype=np.float32)
+    t_a = None if t is None else np.ascontiguousarray(t, dtype=np.float32)
+    dyn_a = None if dyn is None else np.ascontiguousarray(dyn, dtype=np.uint8)
+    k = lib.orc_prune(ctypes.c_long(npts), _ptr(xyz), _ptr(rgb_a), _ptr(t_a), _ptr(dyn_a), ctypes.c_float(inv_s),
+                      ctypes.c_float(inv_d), int(min_support), ctypes.c_long(cap), _ptr(rep), _ptr(cnt), _ptr(cen),
+                      _ptr(mrgb), _ptr(mt), _ptr(flag))
+    if k < 0:
+        raise RuntimeError(f"orc_prune failed ({k})")
+    return dict(rep=rep[:k], count=cnt[:k], centroid=cen[:k], rgb=mrgb[:k], t=mt[:k], flag=flag[:k])
+
+
+def sh_basis(d: np.ndarray) -> np.ndarray:
+    """The 15 real SH basis values of degree 1..3 at unit direction d."""
+    lib = _load()
+    out = np.zeros(15, dtype=np.float64)
+    lib.orc_sh_basis(_ptr(_f64(d)), _ptr(out))
+    return out
+
+
+def cov4(logscale4, ql, qr, mode: int = MODE_FULL) -> np.ndarray:
+    """The 4D covariance R diag(s^2) R^T of one Gaussian -> (4, 4)."""
+    lib = _load()
+    out = np.zeros(16, dtype=np.float64)
+    lib.orc_cov4(int(mode), _ptr(_f64(logscale4)), _ptr(_f64(ql)), _ptr(_f64(qr)), _ptr(out))
+    return out.reshape(4, 4)
