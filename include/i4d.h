@@ -1,0 +1,255 @@
+/*
+ * i4d.h -- C ABI of the GB300 (sm_103a) 4D-Gaussian rasterizer of Instant4D (arXiv 2510.01119).
+ *
+ * The library (libi4d.so) runs the data-parallel hot path of the method's optimisation step:
+ * slicing of native 4D Gaussians at the frame time, EWA projection, tile binning with a device
+ * radix sort, front-to-back compositing, the analytic backward, a fused Adam update, the
+ * photometric loss, and the voxel-grid pruning of the back-projected depth point cloud.
+ *
+ * Conventions for every entry point
+ *   - Tensor arguments are DEVICE pointers owned by the caller, unless a comment says "host".
+ *     The library never allocates device memory: calls that need scratch take a workspace
+ *     pointer and size, with a *_workspace_size() query beside them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only enqueue work: none
+ *     synchronises with the host, so a sequence of calls can be captured into a CUDA graph.
+ *     Counts that the device computes (instances, kept voxels) stay in device memory and the
+ *     kernels that consume them read them there.
+ *   - Return value: I4D_OK, or a negative I4D_ERR_* code for argument errors detected on the
+ *     host and for launch failures.  Conditions only the device can see (capacity overflow)
+ *     are reported through a device status word that the caller reads after the stream work.
+ *   - No call aborts, traps or spins without a bound.
+ *
+ * Data layouts
+ *   Gaussian parameters are ONE flat float32 buffer of (5 + K) planes of N float4 each, where
+ *   K = 0, 3, 6, 12 for SH degree 0..3 (plane p holds floats [4 N p, 4 N (p + 1))):
+ *     plane 0  mean4      (x, y, z, t)                         Sec. 3.3: 4D mean
+ *     plane 1  logscale4  (log s_x, log s_y, log s_z, log s_t) Sec. 3.3: diagonal 4D scale
+ *     plane 2  q_l        (a, b, c, d) = a + bi + cj + dk      Sec. 3.3: 4x4 rotation R = L(q_l) R(q_r)
+ *     plane 3  q_r                                             (two-quaternion form of 4DGS, Sec. 3.1)
+ *     plane 4  (opacity logit, r, g, b)                        Sec. 3.3: opacity and RGB colour
+ *     plane 5+ SH coefficients of degree 1..deg, coefficient k channel c at float 3k + c of the
+ *              Gaussian's SH group, i.e. plane 5 + (3k + c) / 4, lane (3k + c) % 4.
+ *   A 4-vector (x, y, z, t) is the quaternion t + xi + yj + zk; R v = q_l v q_r (normalised q).
+ *   Gradients use the same flat layout.
+ *   Projected records: 3 planes of V x N float4 (view-major within a plane): plane 0 (u, v,
+ *   conic_a, conic_b), plane 1 (conic_c, o_t, r, g), plane 2 (b, depth, radius, 0).
+ *   2D gradients (scratch of the backward): 3 planes of V x N float4: (du, dv, dconic_a,
+ *   dconic_b), (dconic_c, do_t, dr, dg), (db, 0, 0, 0).
+ *   Images: per view, planar float32 [3][H][W]; views concatenated in order.  Per-pixel
+ *   buffers (T_final, last, n_contrib): per view [H][W], concatenated.
+ */
+#ifndef I4D_H
+#define I4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define I4D_API __attribute__((visibility("default")))
+#else
+#define I4D_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define I4D_VERSION 1
+
+#define I4D_OK 0
+#define I4D_ERR_ARG (-1)       /* invalid argument (null pointer, size, alignment, mode) */
+#define I4D_ERR_CAPACITY (-2)  /* an output did not fit its capacity (device status word) */
+#define I4D_ERR_CUDA (-3)      /* a CUDA launch or runtime call failed */
+#define I4D_ERR_WORKSPACE (-4) /* workspace smaller than *_workspace_size() */
+
+#define I4D_MAX_VIEWS 64
+#define I4D_PROJ_FLOATS 12     /* floats per projected record (3 float4 planes) */
+#define I4D_GRAD2D_FLOATS 12   /* floats per (view, Gaussian) 2D-gradient record (3 float4 planes) */
+
+enum { I4D_MODE_FULL = 0, I4D_MODE_ISO_ROT = 1, I4D_MODE_ISO_IDENTITY = 2 };
+enum { I4D_LOSS_L1 = 0, I4D_LOSS_MSE = 1 };
+
+/* One view's camera (DEVICE array of V entries, 80 bytes each).  World->camera pose (R, t) with
+ * OpenCV axes (x right, y down, z forward); pixel centres at (px + 0.5, py + 0.5); time is the
+ * frame time in the scene's normalised time axis. */
+typedef struct {
+  float R[9];   /* row-major */
+  float t[3];
+  float fx, fy, cx, cy;
+  float time;
+  float pad[3];
+} i4d_camera;
+
+/* Host description of a batch of views rendered in one launch. */
+typedef struct {
+  int32_t n_views;                   /* 1..I4D_MAX_VIEWS */
+  int32_t tile_w, tile_h;            /* screen tile; supported: 16x16, 8x8, 16x8, 32x8, 32x16 */
+  int32_t width[I4D_MAX_VIEWS];
+  int32_t height[I4D_MAX_VIEWS];
+} i4d_views;
+
+/* Host struct naming the Gaussian parameters. */
+typedef struct {
+  const float* params;  /* DEVICE, flat layout above, 16-byte aligned */
+  int32_t n;            /* number of Gaussians */
+  int32_t sh_deg;       /* 0..3 */
+  int32_t mode;         /* I4D_MODE_* (Sec. 3.3 "Isotropic Gaussian": ISO modes tie s_x = s_y = s_z
+                           to logscale.x; ISO_IDENTITY also fixes R = I) */
+} i4d_gaussians;
+
+/* Thresholds of the renderer (host).  The paper leaves them to the 3D splatting renderer it
+ * builds on; i4d_default_settings() gives alpha_max 0.99, alpha_min 1/255, T_min 1e-4,
+ * q_max 9 (3-sigma ellipse), ot_min 1/255 (temporal cull, Sec. 3.3), z_near 0.2,
+ * dilation 0.3 px^2, fov_clamp 1.3. */
+typedef struct {
+  float alpha_max, alpha_min, T_min, q_max, ot_min, z_near, dilation, fov_clamp;
+  float bg[3];          /* background colour composited behind the last fragment */
+  float pad;
+} i4d_settings;
+
+/* Launch tuning (host); zeros select defaults. */
+typedef struct {
+  int32_t batch;        /* records staged in shared memory per round (render): 0 = tile pixels */
+  int32_t reserved[7];
+} i4d_tune;
+
+/* One Adam parameter group: floats [begin, end) of the flat buffer; lane = index % 4 selects
+ * lr_init/lr_final; the learning rate decays log-linearly from lr_init to lr_final over
+ * decay_steps updates (constant if decay_steps <= 0). */
+typedef struct {
+  int64_t begin, end;
+  float lr_init[4];
+  float lr_final[4];
+  int32_t decay_steps;
+  int32_t pad;
+} i4d_adam_group;
+
+#define I4D_MAX_ADAM_GROUPS 16
+
+I4D_API int32_t i4d_version(void);
+I4D_API const char* i4d_status_string(int32_t status);
+I4D_API void i4d_default_settings(i4d_settings* out /* host */);
+/* Floats per Gaussian in the flat parameter layout: 20 + 4 K. */
+I4D_API int64_t i4d_param_floats(int32_t sh_deg);
+
+/*
+ * i4d_slice_project -- Eq. 7-8 (conditional mean mu_xyz|t and covariance Sigma_xyz|t of each 4D
+ * Gaussian at each view's frame time), the temporal marginal opacity o_t = sigmoid(o) N(t; mu_t,
+ * Sigma_44) with its cull below settings.ot_min (Sec. 3.3, Eq. 9), EWA projection to 2D, colour
+ * (base RGB + real SH of degree 1..3 of the view direction) and the tile rectangle.
+ *   g        host struct, params on the device
+ *   views    host; cams: DEVICE array of views->n_views cameras
+ *   settings host (NULL = defaults)
+ *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 3-plane record layout
+ *   touched  DEVICE out, n_views * n uint32: number of tiles of the record's rectangle
+ *            (0 for culled or off-screen Gaussians)
+ */
+I4D_API int32_t i4d_slice_project(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,
+                          const i4d_settings* settings, float* proj, uint32_t* touched, void* stream);
+
+/*
+ * i4d_bin_tiles -- the tile binning of the 3D splatting renderer (Sec. 3.1): every (tile,
+ * Gaussian) pair of the touched rectangles gets key ((view tile offset + tile) << 32 | depth
+ * bits), a stable LSD radix sort orders the pairs by (tile, depth, Gaussian id), and each tile's
+ * [start, end) range in the sorted list is found.
+ *   proj, touched  DEVICE in (from i4d_slice_project)
+ *   capacity       size of ids (and of the key arrays in the workspace)
+ *   ids            DEVICE out, capacity uint32: Gaussian id of each sorted pair
+ *   ranges         DEVICE out, 2 * total_tiles uint32 ([start, end) per tile, all views)
+ *   n_inst         DEVICE out, 1 int64: number of pairs (may exceed capacity)
+ *   status         DEVICE out, 1 int32: I4D_OK, or I4D_ERR_CAPACITY when n_inst > capacity
+ *                  (the sorted output is then invalid; retry with capacity >= n_inst)
+ *   ws, ws_bytes   DEVICE workspace, at least i4d_bin_tiles_workspace_size(views, n, capacity)
+ */
+I4D_API size_t i4d_bin_tiles_workspace_size(const i4d_views* views, int32_t n, int64_t capacity);
+I4D_API int32_t i4d_bin_tiles(const i4d_views* views, int32_t n, const float* proj, const uint32_t* touched,
+                      int64_t capacity, uint32_t* ids, uint32_t* ranges, int64_t* n_inst, int32_t* status,
+                      void* ws, size_t ws_bytes, void* stream);
+I4D_API int64_t i4d_total_tiles(const i4d_views* views);
+I4D_API int64_t i4d_total_pixels(const i4d_views* views);
+
+/*
+ * i4d_render_fwd -- front-to-back alpha compositing (the 3D splatting renderer, Sec. 3.1, Eq. 3)
+ * of every view in ONE launch: a Gaussian covers a pixel centre p when q = (p-uv)^T conic (p-uv)
+ * <= q_max; alpha = min(alpha_max, o_t exp(-q/2)); fragments below alpha_min are skipped; the walk
+ * ends before the fragment that would take T below T_min; C = sum T alpha rgb + T_final bg.
+ *   img       DEVICE out, total_pixels * 3 floats (per view planar [3][H][W])
+ *   T_final   DEVICE out, total_pixels floats
+ *   last      DEVICE out, total_pixels uint32: 1 + position (within the tile's range) of the last
+ *             blended fragment (0 if none) -- the backward resumes from here
+ *   n_contrib DEVICE out, total_pixels uint32: fragments blended
+ */
+I4D_API int32_t i4d_render_fwd(const i4d_views* views, int32_t n, const float* proj, const uint32_t* ids,
+                       const uint32_t* ranges, const i4d_settings* settings, const i4d_tune* tune, float* img,
+                       float* T_final, uint32_t* last, uint32_t* n_contrib, void* stream);
+
+/*
+ * i4d_render_bwd -- analytic backward of i4d_render_fwd and i4d_slice_project: back-to-front
+ * per pixel (transmittance recomputed from T_final, no per-fragment state), per-Gaussian 2D
+ * gradients reduced over each warp before the atomics, then the chain through projection,
+ * Eq. 7-8 slicing, the temporal opacity and the 4D parameterisation.
+ *   dL_dimg  DEVICE in, same layout as img
+ *   grad2d   DEVICE scratch, n_views * n * I4D_GRAD2D_FLOATS floats (contents undefined after)
+ *   grads    DEVICE out, flat parameter layout (overwritten; views summed)
+ */
+I4D_API int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,
+                       const i4d_settings* settings, const float* proj, const uint32_t* touched,
+                       const uint32_t* ids, const uint32_t* ranges, const float* T_final, const uint32_t* last,
+                       const float* dL_dimg, float* grad2d, float* grads, void* stream);
+
+/*
+ * i4d_loss -- the single photometric loss of the method (supplementary "Discussion with previous
+ * work": one photometric term; Sec. 4.1: the standard 3DGS loss), L1 or MSE over every pixel and
+ * channel of all views, mean-reduced; writes dL/dimg and the loss value.
+ *   loss_out DEVICE out, 1 float.  target: same layout as img.
+ */
+I4D_API int32_t i4d_loss(const float* img, const float* target, int64_t count, int32_t kind, float* dL_dimg,
+                 float* loss_out, void* stream);
+
+/* i4d_psnr -- 10 log10(1 / MSE) over count floats in [0, 1] (the PSNR of Tables 1-4). */
+I4D_API int32_t i4d_psnr(const float* img, const float* target, int64_t count, float* psnr_out, void* stream);
+
+/*
+ * i4d_adam_step -- fused Adam update over the flat buffer (Sec. 4.1: standard 3DGS optimiser
+ * settings with per-group learning rates, position learning rate 1e-5, decayed over the run).
+ * Reads the update number from *step (DEVICE int32, the count of updates already done), uses
+ * step + 1 for the bias correction and the schedule, and increments *step, so a captured graph
+ * replays correctly.  groups: host array of n_groups (<= I4D_MAX_ADAM_GROUPS).
+ */
+I4D_API int32_t i4d_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
+                      const i4d_adam_group* groups, int32_t n_groups, int32_t* step, float beta1, float beta2,
+                      float eps, void* stream);
+
+/*
+ * i4d_prune_points -- Eq. 5 back-projection of F depth maps (pixel centre, z-depth, camera-space
+ * D K^-1 p, world R^T (X_c - t)) fused with the voxel-grid pruning of Sec. 3.2: voxel index =
+ * floor(float32(x * (1 / S_v))) per axis, the dynamic flag is part of the key (static and dynamic
+ * points never share a voxel, each flag with its own S_v), aggregation in a device hash table
+ * (count, sums in 64-bit fixed point, minimum point index), voxels with fewer than min_support
+ * points dropped, output ordered by representative (minimum) point index.
+ *   depth    DEVICE F*H*W float32;  rgb: DEVICE F*H*W*3 uint8 or NULL;  dyn: F*H*W uint8 or NULL
+ *   cams     DEVICE F cameras (time = frame time)
+ *   outputs  DEVICE, capacity entries each: rep (uint32 point index f*H*W + py*W + px),
+ *            count (int32), xyz (float32 x3 centroid), rgb_out (float32 x3 mean colour in [0,1]),
+ *            t_out (float32 mean time), flag (uint8)
+ *   n_kept   DEVICE out, 1 int64;  status: DEVICE out, 1 int32 (I4D_ERR_CAPACITY when the table or
+ *            the output overflowed)
+ */
+I4D_API size_t i4d_prune_workspace_size(int64_t n_points, int64_t table_slots);
+I4D_API int32_t i4d_prune_points(const float* depth, const uint8_t* rgb, const uint8_t* dyn, const i4d_camera* cams,
+                         int32_t F, int32_t W, int32_t H, float voxel_static, float voxel_dynamic,
+                         int32_t min_support, int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count,
+                         float* xyz, float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
+                         void* ws, size_t ws_bytes, void* stream);
+/* Same pruning on a ready float32 point cloud (xyz n x 3; rgb n x 3 float or NULL; t, dyn or NULL). */
+I4D_API int32_t i4d_prune_points_xyz(const float* xyz, const float* rgb, const float* t, const uint8_t* dyn,
+                             int64_t n_points, float voxel_static, float voxel_dynamic, int32_t min_support,
+                             int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count, float* xyz_out,
+                             float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
+                             void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* I4D_H */

@@ -1,0 +1,301 @@
+// extern "C" entry points of libi4d.so (declared and documented in include/i4d.h).
+// Host-side argument checks happen here; every device buffer is caller-owned.
+#include <string.h>
+
+#include "kernels.cuh"
+
+using namespace i4d;
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+Settings to_settings(const i4d_settings* s) {
+  i4d_settings d;
+  if (!s) {
+    i4d_default_settings(&d);
+    s = &d;
+  }
+  Settings r;
+  r.alpha_max = s->alpha_max;
+  r.alpha_min = s->alpha_min;
+  r.T_min = s->T_min;
+  r.q_max = s->q_max;
+  r.ot_min = s->ot_min;
+  r.z_near = s->z_near;
+  r.dilation = s->dilation;
+  r.fov_clamp = s->fov_clamp;
+  r.bg[0] = s->bg[0];
+  r.bg[1] = s->bg[1];
+  r.bg[2] = s->bg[2];
+  return r;
+}
+
+bool tile_supported(int w, int h) {
+  return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 16 && h == 8) || (w == 32 && h == 8) ||
+         (w == 32 && h == 16);
+}
+
+// Fill the per-launch view table; returns false on invalid views.
+bool make_view_table(const i4d_views* v, ViewTable& vt) {
+  if (!v || v->n_views < 1 || v->n_views > I4D_MAX_VIEWS || !tile_supported(v->tile_w, v->tile_h)) return false;
+  memset(&vt, 0, sizeof(vt));
+  vt.n_views = v->n_views;
+  vt.tile_w = v->tile_w;
+  vt.tile_h = v->tile_h;
+  int64_t toff = 0, poff = 0;
+  for (int k = 0; k < v->n_views; ++k) {
+    const int W = v->width[k], H = v->height[k];
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return false;
+    vt.width[k] = W;
+    vt.height[k] = H;
+    vt.tiles_x[k] = (W + v->tile_w - 1) / v->tile_w;
+    vt.tiles_y[k] = (H + v->tile_h - 1) / v->tile_h;
+    vt.tile_off[k] = (int)toff;
+    vt.pix_off[k] = poff;
+    toff += (int64_t)vt.tiles_x[k] * vt.tiles_y[k];
+    poff += (int64_t)W * H;
+  }
+  if (toff >= (1ll << 31)) return false;
+  vt.tile_off[v->n_views] = (int)toff;
+  vt.pix_off[v->n_views] = poff;
+  return true;
+}
+
+int32_t cuda_status(cudaError_t e) { return e == cudaSuccess ? I4D_OK : I4D_ERR_CUDA; }
+
+int bits_for(int64_t x) {
+  int b = 0;
+  while ((1ll << b) < x) ++b;
+  return b;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t i4d_version(void) { return I4D_VERSION; }
+
+const char* i4d_status_string(int32_t status) {
+  switch (status) {
+    case I4D_OK: return "ok";
+    case I4D_ERR_ARG: return "invalid argument";
+    case I4D_ERR_CAPACITY: return "capacity exceeded";
+    case I4D_ERR_CUDA: return "CUDA error";
+    case I4D_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+void i4d_default_settings(i4d_settings* out) {
+  if (!out) return;
+  out->alpha_max = 0.99f;
+  out->alpha_min = 1.0f / 255.0f;
+  out->T_min = 1e-4f;
+  out->q_max = 9.0f;
+  out->ot_min = 1.0f / 255.0f;
+  out->z_near = 0.2f;
+  out->dilation = 0.3f;
+  out->fov_clamp = 1.3f;
+  out->bg[0] = out->bg[1] = out->bg[2] = 0.0f;
+  out->pad = 0.0f;
+}
+
+int64_t i4d_param_floats(int32_t sh_deg) {
+  if (sh_deg < 0 || sh_deg > 3) return -1;
+  return 20 + 4 * sh_planes(sh_deg);
+}
+
+int64_t i4d_total_tiles(const i4d_views* views) {
+  ViewTable vt;
+  if (!make_view_table(views, vt)) return -1;
+  return vt.tile_off[vt.n_views];
+}
+
+int64_t i4d_total_pixels(const i4d_views* views) {
+  ViewTable vt;
+  if (!make_view_table(views, vt)) return -1;
+  return vt.pix_off[vt.n_views];
+}
+
+int32_t i4d_slice_project(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,
+                          const i4d_settings* settings, float* proj, uint32_t* touched, void* stream) {
+  ViewTable vt;
+  if (!g || g->n < 0 || g->sh_deg < 0 || g->sh_deg > 3 || g->mode < 0 || g->mode > 2) return I4D_ERR_ARG;
+  if (!make_view_table(views, vt)) return I4D_ERR_ARG;
+  if (g->n == 0) return I4D_OK;
+  if (!g->params || !cams || !proj || !touched || !aligned16(g->params) || !aligned16(proj)) return I4D_ERR_ARG;
+  return cuda_status(launch_slice_project(g->params, g->n, g->sh_deg, g->mode, vt, cams, to_settings(settings), proj,
+                                          touched, (cudaStream_t)stream));
+}
+
+size_t i4d_bin_tiles_workspace_size(const i4d_views* views, int32_t n, int64_t capacity) {
+  ViewTable vt;
+  if (!make_view_table(views, vt) || n < 0 || capacity < 0) return 0;
+  const int64_t VN = (int64_t)vt.n_views * n;
+  size_t b = 0;
+  b += align256(4 * (size_t)(VN > 0 ? VN : 1));           // offsets
+  b += align256(scan_workspace_bytes(VN));                  // scan partials
+  b += 2 * align256(8 * (size_t)(capacity > 0 ? capacity : 1));  // keys, keys_alt
+  b += 2 * align256(4 * (size_t)(capacity > 0 ? capacity : 1));  // vals, vals_alt
+  b += align256(radix_workspace_bytes(capacity));
+  return b;
+}
+
+int32_t i4d_bin_tiles(const i4d_views* views, int32_t n, const float* proj, const uint32_t* touched,
+                      int64_t capacity, uint32_t* ids, uint32_t* ranges, int64_t* n_inst, int32_t* status, void* ws,
+                      size_t ws_bytes, void* stream) {
+  ViewTable vt;
+  if (!make_view_table(views, vt) || n < 0 || capacity < 1 || capacity >= (1ll << 32)) return I4D_ERR_ARG;
+  if (!proj || !touched || !ids || !ranges || !n_inst || !status || !ws) return I4D_ERR_ARG;
+  if (ws_bytes < i4d_bin_tiles_workspace_size(views, n, capacity)) return I4D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t VN = (int64_t)vt.n_views * n;
+  char* p = reinterpret_cast<char*>(ws);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(p);
+  p += align256(4 * (size_t)(VN > 0 ? VN : 1));
+  void* scan_ws = p;
+  p += align256(scan_workspace_bytes(VN));
+  uint64_t* keys = reinterpret_cast<uint64_t*>(p);
+  p += align256(8 * (size_t)capacity);
+  uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
+  p += align256(8 * (size_t)capacity);
+  uint32_t* vals = reinterpret_cast<uint32_t*>(p);
+  p += align256(4 * (size_t)capacity);
+  uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
+  p += align256(4 * (size_t)capacity);
+  void* radix_ws = p;
+
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = launch_scan_u32(touched, offs, VN, n_inst, scan_ws, st);
+  if (e == cudaSuccess) e = launch_emit_keys(vt, n, proj, touched, offs, capacity, keys, vals, st);
+  uint64_t* sorted_keys = nullptr;
+  const int bits = 32 + bits_for(vt.tile_off[vt.n_views]);
+  if (e == cudaSuccess)
+    e = launch_radix_sort(keys, vals, keys_alt, vals_alt, ids, capacity, n_inst, bits, radix_ws, &sorted_keys, st);
+  if (e == cudaSuccess)
+    e = launch_tile_ranges(sorted_keys, n_inst, capacity, ranges, vt.tile_off[vt.n_views], status, st);
+  return cuda_status(e);
+}
+
+int32_t i4d_render_fwd(const i4d_views* views, int32_t n, const float* proj, const uint32_t* ids,
+                       const uint32_t* ranges, const i4d_settings* settings, const i4d_tune* tune, float* img,
+                       float* T_final, uint32_t* last, uint32_t* n_contrib, void* stream) {
+  ViewTable vt;
+  if (!make_view_table(views, vt) || n < 0) return I4D_ERR_ARG;
+  if (!proj || !ids || !ranges || !img || !T_final || !last || !n_contrib) return I4D_ERR_ARG;
+  return cuda_status(launch_render_fwd(vt, n, proj, ids, ranges, to_settings(settings), tune ? tune->batch : 0, img,
+                                       T_final, last, n_contrib, (cudaStream_t)stream));
+}
+
+int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,
+                       const i4d_settings* settings, const float* proj, const uint32_t* touched,
+                       const uint32_t* ids, const uint32_t* ranges, const float* T_final, const uint32_t* last,
+                       const float* dL_dimg, float* grad2d, float* grads, void* stream) {
+  ViewTable vt;
+  if (!g || g->n < 0 || g->sh_deg < 0 || g->sh_deg > 3 || g->mode < 0 || g->mode > 2) return I4D_ERR_ARG;
+  if (!make_view_table(views, vt)) return I4D_ERR_ARG;
+  if (g->n == 0) return I4D_OK;
+  if (!g->params || !cams || !proj || !touched || !ids || !ranges || !T_final || !last || !dL_dimg || !grad2d ||
+      !grads || !aligned16(grad2d) || !aligned16(grads))
+    return I4D_ERR_ARG;
+  const Settings S = to_settings(settings);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_render_bwd(vt, g->n, proj, ids, ranges, S, T_final, last, dL_dimg, grad2d, st);
+  if (e == cudaSuccess)
+    e = launch_slice_project_bwd(g->params, g->n, g->sh_deg, g->mode, vt, cams, S, touched, grad2d, grads, st);
+  return cuda_status(e);
+}
+
+int32_t i4d_loss(const float* img, const float* target, int64_t count, int32_t kind, float* dL_dimg,
+                 float* loss_out, void* stream) {
+  if (count < 0 || (kind != I4D_LOSS_L1 && kind != I4D_LOSS_MSE) || !loss_out) return I4D_ERR_ARG;
+  if (count > 0 && (!img || !target || !dL_dimg)) return I4D_ERR_ARG;
+  return cuda_status(launch_loss(img, target, count, kind, dL_dimg, loss_out, (cudaStream_t)stream));
+}
+
+int32_t i4d_psnr(const float* img, const float* target, int64_t count, float* psnr_out, void* stream) {
+  if (count < 0 || !psnr_out || (count > 0 && (!img || !target))) return I4D_ERR_ARG;
+  return cuda_status(launch_psnr(img, target, count, psnr_out, (cudaStream_t)stream));
+}
+
+int32_t i4d_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
+                      const i4d_adam_group* groups, int32_t n_groups, int32_t* step, float beta1, float beta2,
+                      float eps, void* stream) {
+  if (count < 0 || (count & 3) || n_groups < 0 || n_groups > I4D_MAX_ADAM_GROUPS || !step) return I4D_ERR_ARG;
+  if (count > 0 && (!params || !grads || !m || !v || !aligned16(params) || !aligned16(grads) || !aligned16(m) ||
+                    !aligned16(v)))
+    return I4D_ERR_ARG;
+  if (n_groups > 0 && !groups) return I4D_ERR_ARG;
+  AdamGroups G;
+  memset(&G, 0, sizeof(G));
+  G.n = n_groups;
+  for (int k = 0; k < n_groups; ++k) {
+    if (groups[k].begin < 0 || groups[k].end > count || groups[k].begin > groups[k].end || (groups[k].begin & 3) ||
+        (groups[k].end & 3))
+      return I4D_ERR_ARG;
+    G.begin[k] = groups[k].begin;
+    G.end[k] = groups[k].end;
+    for (int l = 0; l < 4; ++l) {
+      G.lr0[k][l] = groups[k].lr_init[l];
+      G.lr1[k][l] = groups[k].lr_final[l];
+    }
+    G.decay[k] = groups[k].decay_steps;
+  }
+  return cuda_status(launch_adam(params, grads, m, v, count, G, step, beta1, beta2, eps, (cudaStream_t)stream));
+}
+
+size_t i4d_prune_workspace_size(int64_t n_points, int64_t table_slots) {
+  if (n_points < 0 || table_slots < 1 || (table_slots & (table_slots - 1))) return 0;
+  return prune_workspace_bytes(n_points, table_slots);
+}
+
+static int32_t prune_common(const float* depth, const uint8_t* rgb8, const uint8_t* dyn, const i4d_camera* cams,
+                            int32_t F, int32_t W, int32_t H, const float* xyz, const float* rgbf, const float* tpt,
+                            int64_t n_points, float voxel_static, float voxel_dynamic, int32_t min_support,
+                            int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count, float* xyz_out,
+                            float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!(voxel_static > 0.0f) || !(voxel_dynamic > 0.0f) || min_support < 1 || capacity < 1 || table_slots < 1 ||
+      (table_slots & (table_slots - 1)) || table_slots >= (1ll << 32))
+    return I4D_ERR_ARG;
+  if (!rep || !count || !xyz_out || !rgb_out || !t_out || !flag || !n_kept || !status || !ws) return I4D_ERR_ARG;
+  if (n_points >= (1ll << 32)) return I4D_ERR_ARG;
+  if (ws_bytes < prune_workspace_bytes(n_points, table_slots)) return I4D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  PruneOut out{rep, count, xyz_out, rgb_out, t_out, flag, n_kept, status};
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  // the voxel index is floor of x times the float32 reciprocal of the voxel size
+  const float inv_s = 1.0f / voxel_static, inv_d = 1.0f / voxel_dynamic;
+  if (e == cudaSuccess)
+    e = launch_prune(depth, rgb8, dyn, cams, F, W, H, xyz, rgbf, tpt, n_points, inv_s, inv_d, min_support,
+                     table_slots, capacity, out, ws, st);
+  return cuda_status(e);
+}
+
+int32_t i4d_prune_points(const float* depth, const uint8_t* rgb, const uint8_t* dyn, const i4d_camera* cams,
+                         int32_t F, int32_t W, int32_t H, float voxel_static, float voxel_dynamic,
+                         int32_t min_support, int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count,
+                         float* xyz, float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
+                         void* ws, size_t ws_bytes, void* stream) {
+  if (F < 0 || W < 0 || H < 0 || !depth || !cams) return I4D_ERR_ARG;
+  const int64_t np = (int64_t)F * W * H;
+  return prune_common(depth, rgb, dyn, cams, F, W, H, nullptr, nullptr, nullptr, np, voxel_static, voxel_dynamic,
+                      min_support, table_slots, capacity, rep, count, xyz, rgb_out, t_out, flag, n_kept, status, ws,
+                      ws_bytes, stream);
+}
+
+int32_t i4d_prune_points_xyz(const float* xyz, const float* rgb, const float* t, const uint8_t* dyn,
+                             int64_t n_points, float voxel_static, float voxel_dynamic, int32_t min_support,
+                             int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count, float* xyz_out,
+                             float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
+                             void* ws, size_t ws_bytes, void* stream) {
+  if (n_points < 0 || (n_points > 0 && !xyz)) return I4D_ERR_ARG;
+  return prune_common(nullptr, nullptr, dyn, nullptr, 0, 0, 0, xyz, rgb, t, n_points, voxel_static, voxel_dynamic,
+                      min_support, table_slots, capacity, rep, count, xyz_out, rgb_out, t_out, flag, n_kept, status,
+                      ws, ws_bytes, stream);
+}
+
+}  // extern "C"

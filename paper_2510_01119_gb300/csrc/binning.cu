@@ -1,0 +1,324 @@
+// Tile binning: exclusive scan of per-record tile counts, key emission, a stable LSD radix sort of
+// (tile << 32 | depth bits, Gaussian id) pairs, and per-tile [start, end) ranges.
+//
+// Every kernel reads the pair count from device memory (never from the host), so the whole
+// binning step can sit inside a captured CUDA graph; grids are sized for the capacity and blocks
+// beyond the live count return at once.
+#include "kernels.cuh"
+
+namespace i4d {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;                       // per thread per round
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+constexpr int kScanMaxBlocks = 1024;
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// block-wide exclusive scan of one value per thread (blockDim.x == 1024); returns the block total
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t x, uint64_t& excl) {
+  __shared__ uint64_t wsum[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t inc = warp_incl_scan(x);
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t s = wsum[lane];
+    const uint64_t si = warp_incl_scan(s);
+    wsum[lane] = si - s;
+    if (lane == 31) wsum[32] = si;
+  }
+  __syncthreads();
+  excl = wsum[warp] + inc - x;
+  const uint64_t total = wsum[32];
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                                                   int64_t chunk, uint64_t* __restrict__ bsum) {
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(lo + chunk, n);
+  uint64_t s = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += in[i];
+  __shared__ uint64_t red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint64_t t = red[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint64_t* __restrict__ bsum, int nb,
+                                                                int64_t* __restrict__ total) {
+  // nb <= kScanMaxBlocks = blockDim.x
+  const uint64_t x = threadIdx.x < nb ? bsum[threadIdx.x] : 0;
+  uint64_t ex;
+  const uint64_t tot = block_excl_scan(x, ex);
+  if (threadIdx.x < nb) bsum[threadIdx.x] = ex;
+  if (threadIdx.x == 0 && total) *total = (int64_t)tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ in,
+                                                                 uint32_t* __restrict__ out, int64_t n, int64_t chunk,
+                                                                 const uint64_t* __restrict__ bsum) {
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(lo + chunk, n);
+  uint64_t carry = bsum[blockIdx.x];
+  for (int64_t base = lo; base < hi; base += kScanTile) {
+    uint32_t v[kScanItems];
+    uint64_t s = 0;
+    const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
+      s += v[k];
+    }
+    uint64_t ex;
+    const uint64_t tot = block_excl_scan(s, ex);
+    uint64_t run = carry + ex;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (i0 + k < hi) out[i0 + k] = (uint32_t)run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+}
+
+void scan_geometry(int64_t n, int& nb, int64_t& chunk) {
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles < 1) tiles = 1;
+  nb = (int)(tiles < kScanMaxBlocks ? tiles : kScanMaxBlocks);
+  const int64_t tiles_per_block = (tiles + nb - 1) / nb;
+  chunk = tiles_per_block * kScanTile;
+  nb = (int)((n + chunk - 1) / chunk);
+  if (nb < 1) nb = 1;
+}
+
+// ---- key emission ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) emit_keys_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
+                                                        const uint32_t* __restrict__ touched,
+                                                        const uint32_t* __restrict__ offsets, int64_t capacity,
+                                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t VN = (int64_t)vt.n_views * n;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= VN) return;
+  const uint32_t cnt = touched[r];
+  if (cnt == 0) return;
+  const int v = (int)(r / n);
+  const uint32_t id = (uint32_t)(r - (int64_t)v * n);
+  const float4 a = proj[r];
+  const float4 c = proj[2 * VN + r];
+  int x0, y0, x1, y1;
+  tile_rect(a.x, a.y, c.z, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+  const uint64_t dbits = (uint64_t)__float_as_uint(c.y);
+  int64_t o = offsets[r];
+  const int base = vt.tile_off[v];
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx) {
+      if (o < capacity) {
+        keys[o] = ((uint64_t)(base + ty * vt.tiles_x[v] + tx) << 32) | dbits;
+        vals[o] = id;
+      }
+      ++o;
+    }
+}
+
+// ---- radix sort ---------------------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;                          // keys per thread
+constexpr int kRsTile = kRsThreads * kRsItems;        // 4096 keys per block
+constexpr int kRsBins = 256;
+
+__device__ __forceinline__ int64_t live_count(const int64_t* n_dev, int64_t capacity) {
+  const int64_t n = *n_dev;
+  return n < capacity ? n : capacity;
+}
+
+__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
+                                                                const int64_t* __restrict__ n_dev, int64_t capacity,
+                                                                int shift, int nblocks, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kRsWarps][kRsBins];
+  for (int k = threadIdx.x; k < kRsWarps * kRsBins; k += kRsThreads) (&h[0][0])[k] = 0;
+  __syncthreads();
+  const int64_t n = live_count(n_dev, capacity);
+  const int64_t lo = (int64_t)blockIdx.x * kRsTile;
+  const int warp = threadIdx.x >> 5;
+  if (lo < n) {
+    const int64_t hi = min(lo + (int64_t)kRsTile, n);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRsThreads) {
+      const uint32_t d = (uint32_t)(keys[i] >> shift) & 0xffu;
+      atomicAdd(&h[warp][d], 1u);
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) s += h[w][d];
+    hist[(int64_t)d * nblocks + blockIdx.x] = s;
+  }
+}
+
+// Stable scatter: warp w ranks the keys of its contiguous 512-key segment in order, using warp-private
+// digit counters; a per-digit exclusive scan over the warps then places each warp's keys after those of
+// the earlier warps, and the scanned histogram places the block after the earlier blocks.
+__global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const int64_t* __restrict__ n_dev, int64_t capacity, int shift, int nblocks,
+    const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t cnt[kRsWarps][kRsBins];
+  const int64_t n = live_count(n_dev, capacity);
+  const int64_t lo = (int64_t)blockIdx.x * kRsTile;
+  if (lo >= n) return;  // uniform per block
+  for (int k = threadIdx.x; k < kRsWarps * kRsBins; k += kRsThreads) (&cnt[0][0])[k] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t seg = lo + (int64_t)warp * (32 * kRsItems);
+  uint64_t key[kRsItems];
+  uint32_t val[kRsItems];
+  uint32_t rank[kRsItems];
+#pragma unroll
+  for (int j = 0; j < kRsItems; ++j) {
+    const int64_t i = seg + j * 32 + lane;
+    const bool ok = i < n;
+    key[j] = ok ? kin[i] : 0ull;
+    val[j] = ok ? vin[i] : 0u;
+    const uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & 0xffu) : 0x100u;  // 256 = padding
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = (d < 256u) ? cnt[warp][d] : 0u;
+    __syncwarp();
+    rank[j] = before + __popc(peers & lt_mask);
+    if (d < 256u && (peers & lt_mask) == 0) cnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive scan over warps, plus the block's global offset
+  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) {
+    uint32_t run = offs[(int64_t)d * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      const uint32_t c = cnt[w][d];
+      cnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRsItems; ++j) {
+    const int64_t i = seg + j * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (uint32_t)(key[j] >> shift) & 0xffu;
+      const uint32_t pos = cnt[warp][d] + rank[j];
+      kout[pos] = key[j];
+      vout[pos] = val[j];
+    }
+  }
+}
+
+// ---- tile ranges ------------------------------------------------------------------------------------------
+__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ n_dev,
+                                   int64_t capacity, uint32_t* __restrict__ ranges, int32_t* __restrict__ status) {
+  const int64_t total = *n_dev;
+  const int64_t n = total < capacity ? total : capacity;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && total > capacity) set_status(status, I4D_ERR_CAPACITY);
+  if (i >= n) return;
+  const uint32_t t = (uint32_t)(keys[i] >> 32);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (int64_t)t] = (uint32_t)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+}
+
+}  // namespace
+
+size_t scan_workspace_bytes(int64_t) { return sizeof(uint64_t) * kScanMaxBlocks; }
+
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st) {
+  uint64_t* bsum = reinterpret_cast<uint64_t*>(ws);
+  int nb;
+  int64_t chunk;
+  scan_geometry(n, nb, chunk);
+  if (n == 0) {
+    if (total) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+    return cudaSuccess;
+  }
+  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, chunk, bsum);
+  scan_top_kernel<<<1, kScanThreads, 0, st>>>(bsum, nb, total);
+  scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n, chunk, bsum);
+  return cudaGetLastError();
+}
+
+size_t radix_workspace_bytes(int64_t capacity) {
+  const int64_t nblocks = (capacity + kRsTile - 1) / kRsTile;
+  const int64_t hist = (int64_t)kRsBins * (nblocks > 0 ? nblocks : 1);
+  size_t b = sizeof(uint32_t) * (size_t)hist;  // histogram, scanned in place
+  b = (b + 255) & ~(size_t)255;
+  b += scan_workspace_bytes(hist);
+  return b;
+}
+
+cudaError_t launch_radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                              uint32_t* vals_out, int64_t capacity, const int64_t* n_dev, int bits, void* ws,
+                              uint64_t** keys_result, cudaStream_t st) {
+  const int64_t nb64 = (capacity + kRsTile - 1) / kRsTile;
+  const int nblocks = (int)(nb64 > 0 ? nb64 : 1);
+  const int64_t hist_n = (int64_t)kRsBins * nblocks;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
+  size_t off = (sizeof(uint32_t) * (size_t)hist_n + 255) & ~(size_t)255;
+  void* scan_ws = reinterpret_cast<char*>(ws) + off;
+  const int passes = (bits + 7) / 8;
+  uint64_t* kb[2] = {keys, keys_alt};
+  uint32_t* vb[2] = {vals, vals_alt};
+  for (int p = 0; p < passes; ++p) {
+    const uint64_t* kin = kb[p & 1];
+    const uint32_t* vin = (p == 0) ? vals : vb[p & 1];
+    uint64_t* kout = kb[(p + 1) & 1];
+    uint32_t* vout = (p == passes - 1) ? vals_out : vb[(p + 1) & 1];
+    radix_hist_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, n_dev, capacity, 8 * p, nblocks, hist);
+    cudaError_t e = launch_scan_u32(hist, hist, hist_n, nullptr, scan_ws, st);
+    if (e != cudaSuccess) return e;
+    radix_scatter_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, capacity, 8 * p, nblocks, hist);
+  }
+  if (keys_result) *keys_result = kb[passes & 1];
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_keys(const ViewTable& vt, int n, const float* proj, const uint32_t* touched,
+                             const uint32_t* offsets, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                             cudaStream_t st) {
+  const int64_t VN = (int64_t)vt.n_views * n;
+  if (VN == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = (VN + threads - 1) / threads;
+  emit_keys_kernel<<<(unsigned)blocks, threads, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), touched,
+                                                         offsets, capacity, keys, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
+                               int64_t total_tiles, int32_t* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, st);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = (capacity + threads - 1) / threads;
+  tile_ranges_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, st>>>(keys, n_dev, capacity, ranges, status);
+  return cudaGetLastError();
+}
+
+}  // namespace i4d

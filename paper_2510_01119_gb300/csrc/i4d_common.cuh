@@ -1,0 +1,86 @@
+// Shared device-side definitions of the sm_103a kernels (no host-visible ABI here; see i4d.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/i4d.h"
+
+#define I4D_HD __host__ __device__ __forceinline__
+#define I4D_D __device__ __forceinline__
+
+namespace i4d {
+
+constexpr int kMaxViews = I4D_MAX_VIEWS;
+
+// Per-launch table of the batch of views, passed by value as a kernel parameter.
+struct ViewTable {
+  int n_views;
+  int tile_w, tile_h;
+  int width[kMaxViews], height[kMaxViews];
+  int tiles_x[kMaxViews], tiles_y[kMaxViews];
+  int tile_off[kMaxViews + 1];   // cumulative tiles over views
+  int64_t pix_off[kMaxViews + 1];  // cumulative pixels over views
+};
+
+struct Settings {
+  float alpha_max, alpha_min, T_min, q_max, ot_min, z_near, dilation, fov_clamp;
+  float bg[3];
+};
+
+// Camera as loaded into registers / shared memory
+struct Cam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float time;
+  float pad[3];
+};
+static_assert(sizeof(Cam) == sizeof(i4d_camera), "camera layout");
+
+I4D_HD int sh_planes(int deg) { return deg == 0 ? 0 : (deg == 1 ? 3 : (deg == 2 ? 6 : 12)); }
+I4D_HD int sh_coeffs(int deg) { return (deg + 1) * (deg + 1) - 1; }
+
+// Which view owns a global tile index (linear scan: at most 64 views, uniform across a block).
+I4D_D int view_of_tile(const ViewTable& vt, int tile) {
+  int v = 0;
+  while (v + 1 < vt.n_views && tile >= vt.tile_off[v + 1]) ++v;
+  return v;
+}
+
+// Tile rectangle [x0, x1) x [y0, y1) of the square of half-width `radius` around (u, v).
+// The same function is used when counting and when emitting, so both agree bit for bit.
+I4D_D void tile_rect(float u, float v, float radius, int tile_w, int tile_h, int tiles_x, int tiles_y,
+                     int& x0, int& y0, int& x1, int& y1) {
+  const float fx0 = floorf((u - radius) / (float)tile_w);
+  const float fx1 = floorf((u + radius) / (float)tile_w) + 1.0f;
+  const float fy0 = floorf((v - radius) / (float)tile_h);
+  const float fy1 = floorf((v + radius) / (float)tile_h) + 1.0f;
+  x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)tiles_x);
+  x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)tiles_x);
+  y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)tiles_y);
+  y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)tiles_y);
+}
+
+// Fragment evaluation shared by the forward and the backward compositing kernels: q, the
+// Gaussian falloff G = exp(-q/2) and the raw alpha o_t G.  Returns false when the fragment is
+// skipped (outside the q_max ellipse or alpha below alpha_min).  Both kernels call exactly this
+// code on the same inputs, so they take the same decisions.
+I4D_D bool eval_fragment(float dx, float dy, float ca, float cb, float cc, float ot, const Settings& s, float& q,
+                         float& G, float& a_raw, float& alpha) {
+  // explicit roundings: no compiler contraction can make the two kernels differ
+  q = __fmaf_rn(cc, __fmul_rn(dy, dy),
+                __fmaf_rn(__fmul_rn(2.0f, cb), __fmul_rn(dx, dy), __fmul_rn(ca, __fmul_rn(dx, dx))));
+  if (!(q <= s.q_max)) return false;
+  G = __expf(__fmul_rn(-0.5f, q));
+  a_raw = __fmul_rn(ot, G);
+  alpha = fminf(s.alpha_max, a_raw);
+  return alpha >= s.alpha_min;
+}
+
+// device status / error word helpers
+I4D_D void set_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace i4d

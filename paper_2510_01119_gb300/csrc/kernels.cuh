@@ -1,0 +1,68 @@
+// Internal launchers of the sm_103a kernels (called by the C ABI in api.cu).
+#pragma once
+
+#include "i4d_common.cuh"
+
+namespace i4d {
+
+cudaError_t launch_slice_project(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
+                                 const i4d_camera* cams, const Settings& S, float* proj, uint32_t* touched,
+                                 cudaStream_t st);
+cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
+                                     const i4d_camera* cams, const Settings& S, const uint32_t* touched,
+                                     const float* grad2d, float* grads, cudaStream_t st);
+
+// exclusive scan of n uint32 into out (may alias in); the total goes to *total (int64, device)
+size_t scan_workspace_bytes(int64_t n);
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st);
+
+// stable LSD radix sort of (key, value) pairs on bits [0, bits); the count is min(*n_dev, capacity)
+size_t radix_workspace_bytes(int64_t capacity);
+cudaError_t launch_radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                              uint32_t* vals_out, int64_t capacity, const int64_t* n_dev, int bits, void* ws,
+                              uint64_t** keys_result, cudaStream_t st);
+
+cudaError_t launch_emit_keys(const ViewTable& vt, int n, const float* proj, const uint32_t* touched,
+                             const uint32_t* offsets, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                             cudaStream_t st);
+cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
+                               int64_t total_tiles, int32_t* status, cudaStream_t st);
+
+cudaError_t launch_render_fwd(const ViewTable& vt, int n, const float* proj, const uint32_t* ids,
+                              const uint32_t* ranges, const Settings& S, int batch, float* img, float* T_final,
+                              uint32_t* last, uint32_t* n_contrib, cudaStream_t st);
+cudaError_t launch_render_bwd(const ViewTable& vt, int n, const float* proj, const uint32_t* ids,
+                              const uint32_t* ranges, const Settings& S, const float* T_final, const uint32_t* last,
+                              const float* dL_dimg, float* grad2d, cudaStream_t st);
+
+cudaError_t launch_loss(const float* img, const float* target, int64_t count, int kind, float* dL_dimg,
+                        float* loss_out, cudaStream_t st);
+cudaError_t launch_psnr(const float* img, const float* target, int64_t count, float* psnr_out, cudaStream_t st);
+
+struct AdamGroups {
+  int n;
+  int64_t begin[I4D_MAX_ADAM_GROUPS], end[I4D_MAX_ADAM_GROUPS];
+  float lr0[I4D_MAX_ADAM_GROUPS][4], lr1[I4D_MAX_ADAM_GROUPS][4];
+  int decay[I4D_MAX_ADAM_GROUPS];
+};
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamGroups& groups,
+                        int32_t* step, float b1, float b2, float eps, cudaStream_t st);
+
+// grid pruning
+size_t prune_workspace_bytes(int64_t n_points, int64_t table_slots);
+struct PruneOut {
+  uint32_t* rep;
+  int32_t* count;
+  float* xyz;
+  float* rgb;
+  float* t;
+  uint8_t* flag;
+  int64_t* n_kept;
+  int32_t* status;
+};
+cudaError_t launch_prune(const float* depth, const uint8_t* rgb8, const uint8_t* dyn, const i4d_camera* cams, int F,
+                         int W, int H, const float* xyz, const float* rgbf, const float* tpt, int64_t n_points,
+                         float inv_static, float inv_dynamic, int min_support, int64_t table_slots, int64_t capacity,
+                         const PruneOut& out, void* ws, cudaStream_t st);
+
+}  // namespace i4d

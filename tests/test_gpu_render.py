@@ -1,0 +1,258 @@
+"""GPU <-> FP64 oracle parity of slice/project, tile binning, compositing and the backward,
+through the C ABI (libi4d.so)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import (FLAG_MARGIN, GRAD_TOL, IMG_TOL, compare_images, oracle_views, rel_l2,
+                      suspicious_gaussians, tile_pairs_oracle)
+
+pytestmark = pytest.mark.gpu
+
+GRAD_KEYS = ("mean4", "logscale4", "ql", "qr", "opacity", "rgb", "sh")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    from paper_2510_01119_gb300 import build, _lib
+    build.build()
+    _lib.load()
+    assert torch.cuda.is_available()
+    return torch.device("cuda:0")
+
+
+def _gpu_render(g, cams, tile=(16, 16), settings=None, capacity=None):
+    from paper_2510_01119_gb300 import rasterizer as R
+    rast = R.Rasterizer(g["mean4"].shape[0], g["sh_deg"], g.get("mode", 0), [(c["W"], c["H"]) for c in cams],
+                        tile=tile, settings=settings, capacity=capacity)
+    params = R.pack_params(g)
+    camt = R.cameras_tensor(cams)
+    rast.forward(params, camt)
+    return rast, params, camt
+
+
+def _oracle_grads(orc, g, cams, gimgs, settings=None):
+    tot = None
+    for cam, gi in zip(cams, gimgs):
+        _, gr = orc.render_bwd(g, cam, gi.reshape(-1, 3), settings=settings)
+        tot = gr if tot is None else {k: tot[k] + gr[k] for k in tot}
+    return tot
+
+
+def _compare_grads(rast, g, want):
+    from paper_2510_01119_gb300 import rasterizer as R
+    got = R.unpack_params(rast.grads, g["mean4"].shape[0], g["sh_deg"])
+    got["opacity"] = got["opacity"]
+    errs = {}
+    for k in GRAD_KEYS:
+        if k == "sh" and g["sh_deg"] == 0:
+            continue
+        if np.linalg.norm(want[k]) == 0 and np.linalg.norm(got[k]) == 0:
+            continue
+        errs[k] = rel_l2(got[k], want[k])
+    return errs
+
+
+def _settings_dict(orc_settings_over):
+    return orc_settings_over
+
+
+# --------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode,deg", [(0, 0), (1, 0), (2, 0), (0, 3)])
+def test_slice_project_records_match_oracle(dev, orc, mode, deg):
+    g = synth.gaussians_uniform(0, sh_deg=deg, mode=mode)
+    cam = synth.camera(128, 96, 60.0, time=0.5)
+    rast, _, _ = _gpu_render(g, [cam])
+    n = g["mean4"].shape[0]
+    planes = rast.proj.view(3, n, 4).cpu().numpy()
+    touched = rast.touched[:n].cpu().numpy()
+    P = orc.project(g, cam)
+    C = orc.P
+    vis = P[:, C["visible"]] != 0
+    sus = suspicious_gaussians(orc, [P])[0]
+    ok = np.array([i not in sus for i in range(n)])
+    # visibility and tile counts agree except at flagged decisions
+    area = (P[:, C["x1"]] - P[:, C["x0"]]) * (P[:, C["y1"]] - P[:, C["y0"]])
+    want_touched = np.where(vis, area, 0)
+    assert np.array_equal(touched[ok], want_touched[ok])
+    m = vis & ok
+    assert m.sum() > 500
+    u, v, ca, cb = planes[0, m].T
+    cc, ot, r, gg = planes[1, m].T
+    b, depth, radius, _ = planes[2, m].T
+    assert np.allclose(u, P[m, C["u"]], rtol=0, atol=2e-3)
+    assert np.allclose(v, P[m, C["v"]], rtol=0, atol=2e-3)
+    assert np.allclose(depth, P[m, C["depth"]], rtol=2e-6)
+    assert np.allclose(ot, P[m, C["ot"]], rtol=2e-5, atol=1e-7)
+    scale = np.maximum(np.abs(P[m][:, [C["ca"], C["cb"], C["cc"]]]).max(axis=1), 1e-12)
+    for got, col in ((ca, "ca"), (cb, "cb"), (cc, "cc")):
+        assert np.all(np.abs(got - P[m, C[col]]) <= 2e-4 * scale)
+    for got, col in ((r, "r"), (gg, "g"), (b, "b")):
+        assert np.allclose(got, P[m, C[col]], atol=2e-6)
+    assert np.array_equal(radius, P[m, C["radius"]])
+
+
+def test_tile_lists_match_oracle_exactly(dev, orc):
+    g = synth.gaussians_uniform(0)
+    cams = [synth.camera(128, 96, 60.0, time=0.5), synth.camera(75, 41, 55.0, time=0.3)]
+    rast, _, _ = _gpu_render(g, cams)
+    tiles, ids = rast.tile_lists()
+    Ps = [orc.project(g, c) for c in cams]
+    wt, wi = tile_pairs_oracle(orc, Ps, cams)
+    if len(tiles) == len(wt) and np.array_equal(tiles, wt) and np.array_equal(ids, wi):
+        return
+    # only pairs of flagged Gaussians may differ
+    sus = suspicious_gaussians(orc, Ps)
+    n0 = cams[0]["W"]
+    tiles_per_view0 = ((128 + 15) // 16) * ((96 + 15) // 16)
+
+    def keep(t, i):
+        v = 0 if t < tiles_per_view0 else 1
+        return i not in sus[v]
+
+    a = [(t, i) for t, i in zip(tiles, ids) if keep(t, i)]
+    b = [(t, i) for t, i in zip(wt, wi) if keep(t, i)]
+    assert a == b
+    assert sum(len(s) for s in sus) < 20, n0
+
+
+@pytest.mark.parametrize("mode,deg", [(0, 0), (1, 0), (2, 0), (0, 3)])
+def test_render_forward_matches_oracle(dev, orc, mode, deg):
+    g = synth.gaussians_uniform(0, sh_deg=deg, mode=mode)
+    cams = [synth.camera(128, 96, 60.0, time=0.5)]
+    rast, _, _ = _gpu_render(g, cams)
+    ov = oracle_views(orc, g, cams)
+    gimg = [x.cpu().numpy() for x in rast.split_images()]
+    bad, flagged, worst = compare_images(gimg, ov)
+    assert bad == 0, (bad, flagged, worst)
+    assert flagged < 0.03 * 128 * 96
+    T = rast.split_pixels(rast.T_final)[0].cpu().numpy()
+    nc = rast.split_pixels(rast.n_contrib)[0].cpu().numpy()
+    fl = ov[0][4] < FLAG_MARGIN
+    assert np.abs(T - ov[0][2])[~fl].max() < IMG_TOL
+    assert np.array_equal(nc[~fl], ov[0][3][~fl])
+
+
+def test_render_backward_matches_oracle(dev, orc):
+    """MSE against a uniform-random target (the 2,000-Gaussian workload), dL/dimg from the oracle's
+    image and zeroed at flagged pixels (both sides get the same upstream gradient)."""
+    g = synth.gaussians_uniform(0)
+    cam = synth.camera(128, 96, 60.0, time=0.5)
+    rast, params, camt = _gpu_render(g, [cam])
+    ov = oracle_views(orc, g, [cam])
+    img = ov[0][1]
+    tgt = synth.random_image(0, 128, 96)
+    gimg = 2.0 * (img - tgt) / img.size
+    gimg[ov[0][4] < FLAG_MARGIN] = 0.0
+    import torch
+    dl = torch.from_numpy(gimg.transpose(2, 0, 1).astype(np.float32).reshape(-1)).to(dev)
+    rast.backward(params, camt, dl)
+    want = _oracle_grads(orc, g, [cam], [gimg])
+    errs = _compare_grads(rast, g, want)
+    assert all(e < GRAD_TOL for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("mode,deg", [(1, 0), (2, 0), (0, 3)])
+def test_render_backward_modes_and_sh(dev, orc, mode, deg):
+    g = synth.gaussians_uniform(4, n=1500, sh_deg=deg, mode=mode)
+    cam = synth.camera(96, 80, 60.0, time=0.42)
+    rast, params, camt = _gpu_render(g, [cam])
+    ov = oracle_views(orc, g, [cam])
+    gimg = np.random.default_rng(9).normal(size=ov[0][1].shape) * 1e-3
+    gimg[ov[0][4] < FLAG_MARGIN] = 0.0
+    import torch
+    dl = torch.from_numpy(gimg.transpose(2, 0, 1).astype(np.float32).reshape(-1)).to(dev)
+    rast.backward(params, camt, dl)
+    errs = _compare_grads(rast, g, _oracle_grads(orc, g, [cam], [gimg]))
+    assert all(e < GRAD_TOL for e in errs.values()), errs
+
+
+def test_multiview_single_launch_matches_per_view_oracle(dev, orc):
+    """Views at different timestamps and resolutions (ragged sizes) in one launch."""
+    g = synth.gaussians_uniform(0)
+    cams = [synth.camera(128, 96, 60.0, time=0.5), synth.camera(77, 45, 50.0, time=0.1),
+            synth.arc_camera(40, 200, 100, 60), synth.camera(33, 129, 40.0, time=0.9)]
+    rast, params, camt = _gpu_render(g, cams)
+    ov = oracle_views(orc, g, cams)
+    gimg = [x.cpu().numpy() for x in rast.split_images()]
+    bad, flagged, worst = compare_images(gimg, ov)
+    assert bad == 0, (bad, flagged, worst)
+    rng = np.random.default_rng(3)
+    ups = []
+    for (P, img, T, nc, mg) in ov:
+        u = rng.normal(size=img.shape) * 1e-3
+        u[mg < FLAG_MARGIN] = 0.0
+        ups.append(u)
+    import torch
+    dl = torch.from_numpy(np.concatenate([u.transpose(2, 0, 1).reshape(-1) for u in ups]).astype(np.float32)).to(dev)
+    rast.backward(params, camt, dl)
+    errs = _compare_grads(rast, g, _oracle_grads(orc, g, cams, ups))
+    assert all(e < GRAD_TOL for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 8), (32, 8), (32, 16)])
+def test_image_is_tile_size_invariant(dev, orc, tile):
+    g = synth.gaussians_uniform(0)
+    cams = [synth.camera(128, 96, 60.0, time=0.5)]
+    r16, _, _ = _gpu_render(g, cams)
+    rt, _, _ = _gpu_render(g, cams, tile=tile)
+    a = r16.img.cpu().numpy()
+    b = rt.img.cpu().numpy()
+    ov = oracle_views(orc, g, cams)
+    bad, _, _ = compare_images([x.cpu().numpy() for x in rt.split_images()], ov)
+    assert bad == 0
+    assert np.abs(a - b).max() < 1e-5
+
+
+def test_empty_and_fully_culled_scenes(dev, orc):
+    g = synth.gaussians_uniform(0, n=50)
+    g["mean4"][:, 2] = -5.0                      # every Gaussian behind the camera
+    cams = [synth.camera(40, 30, time=0.5)]
+    rast, params, camt = _gpu_render(g, cams)
+    assert int(rast.n_inst.item()) == 0
+    img = rast.img.cpu().numpy()
+    assert np.all(img == 0.0) and np.all(rast.T_final.cpu().numpy() == 1.0)
+    import torch
+    rast.backward(params, camt, torch.ones_like(rast.img))
+    assert np.all(rast.grads.cpu().numpy() == 0.0)
+
+
+def test_capacity_overflow_is_reported_and_recovered(dev, orc):
+    import torch
+    from paper_2510_01119_gb300 import rasterizer as R
+    g = synth.gaussians_uniform(0)
+    cams = [synth.camera(128, 96, 60.0, time=0.5)]
+    rast = R.Rasterizer(2000, 0, 0, [(128, 96)], capacity=1000)
+    params = R.pack_params(g)
+    camt = R.cameras_tensor(cams)
+    rast.project(params, camt)
+    rast.bin()
+    torch.cuda.synchronize()
+    assert int(rast.status.item()) == -2 and int(rast.n_inst.item()) > 1000
+    rast.forward(params, camt)                    # regrows the bins
+    assert rast.capacity >= int(rast.n_inst.item())
+    bad, _, _ = compare_images([x.cpu().numpy() for x in rast.split_images()], oracle_views(orc, g, cams))
+    assert bad == 0
+
+
+def test_autograd_function_matches_oracle(dev, orc):
+    import torch
+    from paper_2510_01119_gb300 import rasterizer as R
+    g = synth.gaussians_uniform(6, n=800)
+    cam = synth.camera(64, 48, 60.0, time=0.55)
+    rast = R.Rasterizer(800, 0, 0, [(64, 48)])
+    params = R.pack_params(g).requires_grad_(True)
+    camt = R.cameras_tensor([cam])
+    img = R.render(params, camt, rast)
+    w = torch.from_numpy(np.random.default_rng(2).normal(size=img.shape[0]).astype(np.float32)).to(dev)
+    ov = oracle_views(orc, g, [cam])
+    fl = ov[0][4] < FLAG_MARGIN
+    wnp = w.cpu().numpy().reshape(3, 48, 64)
+    wnp[:, fl] = 0.0
+    w = torch.from_numpy(wnp.reshape(-1)).to(dev)
+    (img * w).sum().backward()
+    want = _oracle_grads(orc, g, [cam], [wnp.transpose(1, 2, 0).astype(np.float64)])
+    got = R.unpack_params(params.grad, 800, 0)
+    for k in ("mean4", "logscale4", "ql", "qr", "opacity", "rgb"):
+        assert rel_l2(got[k], want[k]) < GRAD_TOL, k
