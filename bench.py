@@ -1,0 +1,514 @@
+#!/usr/bin/env python3
+"""Training-step throughput of the GB300 4D-Gaussian rasterizer (Instant4D, arXiv 2510.01119).
+
+Workload: a seeded 200-frame 640x360 depth video of a room with three moving spheres (46.08 M
+back-projected points) is pruned on a 0.01 voxel grid to ~1.13 M 4D Gaussians (heuristic init);
+one step renders a batch of 8 views at distinct frame times (4 x 960x540 + 4 x 480x270) forward
+and backward through the rasterizer, takes an L1 loss against targets rendered from a hidden
+seeded 4D Gaussian scene of the same room, and applies a fused Adam update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--eager]
+
+One JSON line on stdout (rank 0).  Under torchrun each rank runs an independent replica on its
+own GPU (the step has no cross-GPU exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train it/s (fwd+bwd+Adam, 1M 4DGS, 960x540)"
+N_FRAMES, VIDEO_W, VIDEO_H = 200, 640, 360
+FULL, HALF = (960, 540), (480, 270)
+N_FULL, N_HALF = 4, 4
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--eager", action="store_true", help="launch the step eagerly instead of a CUDA graph")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=4)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed replicas
+# ------------------------------------------------------------------------------------------------
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------------
+def make_video():
+    import synth
+    return synth.depth_video(2, n_frames=N_FRAMES, W=VIDEO_W, H=VIDEO_H)
+
+
+def step_batches(n_steps: int, seed: int = 3):
+    """Frame indices of each step's 4 full-resolution and 4 half-resolution views (distinct times)."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_steps):
+        f = r.choice(N_FRAMES, N_FULL + N_HALF, replace=False)
+        out.append((f[:N_FULL], f[N_FULL:]))
+    return out
+
+
+def build_gpu_workload(dev, vid):
+    import torch
+
+    import synth
+    from paper_2510_01119_gb300 import _lib as L
+    from paper_2510_01119_gb300 import rasterizer as R
+    from paper_2510_01119_gb300 import train as T
+    from paper_2510_01119_gb300.prune import Pruner
+
+    F = vid["depth"].shape[0]
+    depth = torch.from_numpy(vid["depth"]).to(dev)
+    rgb = torch.from_numpy(vid["rgb"]).to(dev)
+    dyn = torch.from_numpy(vid["dyn"]).to(dev)
+    cams = R.cameras_tensor(vid["cams"], dev)
+    pr = Pruner(F * VIDEO_W * VIDEO_H, 1 << 22, capacity=1 << 22, device=dev)
+    prune_ms = []
+    for _ in range(3):  # first run warms up; report the best of the rest
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = pr.prune_depth(depth, rgb, dyn, cams, synth.PRUNE_VOXEL, synth.PRUNE_VOXEL, synth.PRUNE_MIN_SUPPORT)
+        e1.record()
+        torch.cuda.synchronize()
+        prune_ms.append(e0.elapsed_time(e1))
+    if int(out["status"].item()) != 0:
+        raise RuntimeError("pruning overflowed its table")
+    n = int(out["n_kept"].item())
+    params = torch.empty(5 * n * 4, dtype=torch.float32, device=dev)
+    st_dyn, st_static = T.temporal_scales(N_FRAMES)
+    L.i4d_init_heuristic(out["xyz"], out["rgb"], out["t"], out["flag"], n, 0, T.scale_for_voxel(synth.PRUNE_VOXEL),
+                         st_dyn, st_static, 0.1, params)
+    del pr, depth, rgb, dyn
+    # target bank: the hidden scene rendered at every frame of the arc, at both resolutions
+    hidden = synth.room_gaussians(1003, 200000)
+    hp = R.pack_params(hidden, dev)
+    bank = {}
+    for size in (FULL, HALF):
+        W, H = size
+        imgs = torch.empty(N_FRAMES, 3 * W * H, dtype=torch.float32, device=dev)
+        hr = R.Rasterizer(hidden["mean4"].shape[0], 0, 0, [size] * 8, device=dev)
+        for k0 in range(0, N_FRAMES, 8):
+            ks = list(range(k0, min(k0 + 8, N_FRAMES)))
+            ks += [ks[-1]] * (8 - len(ks))
+            ct = R.cameras_tensor([synth.arc_camera(k, N_FRAMES, W, H) for k in ks], dev)
+            img = hr.forward(hp, ct)
+            for j, k in enumerate(ks):
+                imgs[k] = img[j * 3 * W * H:(j + 1) * 3 * W * H]
+        bank[size] = imgs
+        del hr
+    cam_bank = {size: R.cameras_tensor([synth.arc_camera(k, N_FRAMES, size[0], size[1]) for k in range(N_FRAMES)],
+                                       dev) for size in (FULL, HALF)}
+    return dict(n=n, params=params, prune_ms=min(prune_ms[1:]), bank=bank, cam_bank=cam_bank,
+                n_dynamic=int(out["flag"][:n].sum().item()))
+
+
+def algorithmic_bytes(kernel: str, n: int, V: int, I: int, R_vis: int, P: int, passes: int) -> float:
+    """HBM bytes one launch of `kernel` must move at minimum (per-unit figures times the units)."""
+    if kernel == "render_fwd":      # ids 4/instance, record 36/visible record, outputs 24/pixel
+        return 4.0 * I + 36.0 * R_vis + 24.0 * P
+    if kernel == "render_bwd":      # ids, records, 2D-grad atomics 36/visible record, inputs 20/pixel
+        return 4.0 * I + 72.0 * R_vis + 20.0 * P
+    if kernel == "slice_project":   # 80 B params once, 52 B written per (view, Gaussian)
+        return 80.0 * n + 52.0 * V * n
+    if kernel == "slice_project_bwd":  # params 80, touched 4/(view, Gaussian), 2D grads 36/visible, grads 80
+        return 160.0 * n + 4.0 * V * n + 36.0 * R_vis
+    if kernel == "radix_scatter":   # read key+value, write key+value
+        return 24.0 * I
+    if kernel == "radix_hist":
+        return 8.0 * I
+    if kernel == "emit_keys":
+        return 12.0 * I + 4.0 * V * n + 12.0 * R_vis
+    if kernel == "adam":            # p, g, m, v read; p, m, v written
+        return 28.0 * 20 * n
+    if kernel == "loss":
+        return 12.0 * 3 * P
+    return float("nan")
+
+
+# kernels per profiled scope (memsets are not kernels; one scan scope launches three kernels)
+KERNELS_PER_SCOPE = {"scan": 3, "grad2d_clear": 0, "adam": 2, "loss": 1}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_01119_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and workload, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_train_step_1M.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------------
+def oracle_workload(vid):
+    import oracle
+    import synth
+    pts = np.concatenate([oracle.backproject(c, vid["depth"][f]) for f, c in enumerate(vid["cams"])]).astype(np.float32)
+    rgb = vid["rgb"].reshape(-1, 3).astype(np.float32) / 255.0
+    t = np.repeat(vid["times"], VIDEO_W * VIDEO_H).astype(np.float32)
+    t0 = time.perf_counter()
+    res = oracle.prune(pts, synth.PRUNE_VOXEL, synth.PRUNE_VOXEL, synth.PRUNE_MIN_SUPPORT, rgb=rgb, t=t,
+                       dyn=vid["dyn"].reshape(-1))
+    prune_s = time.perf_counter() - t0
+    g = oracle.init_heuristic(res, 0.5 * synth.PRUNE_VOXEL, 2.0 / (N_FRAMES - 1), 1.0)
+    return g, prune_s
+
+
+def oracle_step_sample(g, frames_full, frames_half, px_per_view: int, seed: int):
+    """Oracle projection of all Gaussians + fwd+bwd of px_per_view random pixels, for one full- and
+    one half-resolution view; returns the extrapolated seconds of one full 8-view step."""
+    import oracle
+    import synth
+    r = np.random.default_rng(seed)
+    per_view = {}
+    for size, fr in ((FULL, frames_full[0]), (HALF, frames_half[0])):
+        W, H = size
+        cam = synth.arc_camera(int(fr), N_FRAMES, W, H)
+        pix = r.integers(0, W * H, px_per_view)
+        t0 = time.perf_counter()
+        P = oracle.project(g, cam)
+        t1 = time.perf_counter()
+        oracle.render(P, cam, pix=pix)
+        t2 = time.perf_counter()
+        oracle.render_bwd(g, cam, np.full((px_per_view, 3), 1e-3), pix=pix)
+        t3 = time.perf_counter()
+        # render_bwd repeats the projection and the per-pixel gather internally
+        per_view[size] = (t1 - t0) + (t2 - t1) * (W * H / px_per_view) + (t3 - t2) * (W * H / px_per_view)
+    n = g["mean4"].shape[0]
+    t0 = time.perf_counter()
+    pz = np.zeros(n * 20)
+    oracle.adam_step(pz, pz, pz, pz, 1e-3, 1)
+    t_adam = time.perf_counter() - t0
+    return N_FULL * per_view[FULL] + N_HALF * per_view[HALF] + t_adam
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the oracle as it stands on the host cores, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    vid = make_video()
+    g, prune_s = oracle_workload(vid)
+    batches = step_batches(args.warmup + args.steps)
+    px = 16
+    for k in range(args.warmup):
+        oracle_step_sample(g, *batches[k], px, k)
+    est = []
+    for k in range(args.steps):
+        est.append(oracle_step_sample(g, *batches[args.warmup + k], px, 1000 + k))
+    sec = float(np.mean(est))
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "train_step_1M_8views", "n_gaussians": int(g["mean4"].shape[0]),
+                       "views": "4x960x540+4x480x270", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "it/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"per step: oracle projection of all Gaussians + fwd+bwd of {px} random "
+                                       f"pixels in one 960x540 and one 480x270 view, extrapolated linearly to "
+                                       f"all pixels of the 8-view batch (the oracle is O(pixels x Gaussians))",
+                             "prune_s": prune_s},
+            "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2510_01119_gb300 import _lib as L
+    from paper_2510_01119_gb300 import build as B
+    from paper_2510_01119_gb300 import train as T
+
+    B.build()
+    L.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    vid = make_video()
+    wl = build_gpu_workload(dev, vid)
+    n = wl["n"]
+    sizes = T.sizes_for_batch(FULL, HALF, N_FULL, N_HALF)
+    V = len(sizes)
+    total_steps = args.warmup + args.steps
+    step = T.TrainStep(wl["params"], n, 0, 0, sizes, steps=max(total_steps, 2000), loss_kind=L.LOSS_L1,
+                       capacity=16 * n)
+    batches = step_batches(total_steps + args.profile_steps)
+    fullpix, halfpix = 3 * FULL[0] * FULL[1], 3 * HALF[0] * HALF[1]
+    tgt_full = step.target[:N_FULL * fullpix].view(N_FULL, fullpix)
+    tgt_half = step.target[N_FULL * fullpix:].view(N_HALF, halfpix)
+    idx_dev = [(torch.from_numpy(np.asarray(a, np.int64)).to(dev), torch.from_numpy(np.asarray(b, np.int64)).to(dev))
+               for a, b in batches]
+
+    def load_batch(k):
+        fa, fb = idx_dev[k]
+        torch.index_select(wl["bank"][FULL], 0, fa, out=tgt_full)
+        torch.index_select(wl["bank"][HALF], 0, fb, out=tgt_half)
+        step.cams[:N_FULL].copy_(wl["cam_bank"][FULL].index_select(0, fa))
+        step.cams[N_FULL:].copy_(wl["cam_bank"][HALF].index_select(0, fb))
+
+    # size the bins from a few batches (the captured graph cannot regrow them), with 50% headroom
+    peak = 0
+    for k in range(0, len(batches), max(len(batches) // 6, 1)):
+        load_batch(k)
+        step.rast.project(step.params, step.cams)
+        step.rast.bin()
+        peak = max(peak, int(step.rast.n_inst.item()))
+    step.rast._alloc_bins(int(1.5 * peak) + 4096)
+    load_batch(0)
+    step.rast.forward(step.params, step.cams, check_capacity=True)
+    torch.cuda.synchronize()
+    if not args.eager:
+        step.capture(warmup=1)
+    run = step.run if args.eager else step.replay
+    for k in range(args.warmup):
+        load_batch(k)
+        run()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for k in range(args.steps):
+        load_batch(args.warmup + k)
+        run()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms, ws)
+    overflow = step.overflowed()
+
+    # e2e through host buffers: H2D of the step's targets and cameras from pinned memory, D2H of the loss
+    pool = 4
+    host_tgt = [torch.empty(step.target.numel(), dtype=torch.float32).pin_memory() for _ in range(pool)]
+    host_cam = [torch.empty(V, 20, dtype=torch.float32).pin_memory() for _ in range(pool)]
+    for j in range(pool):
+        load_batch(j)
+        host_tgt[j].copy_(step.target)
+        host_cam[j].copy_(step.cams)
+    host_loss = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    e0.record()
+    for k in range(args.steps):
+        step.target.copy_(host_tgt[k % pool], non_blocking=True)
+        step.cams.copy_(host_cam[k % pool], non_blocking=True)
+        run()
+        host_loss[k:k + 1].copy_(step.loss, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_host1 = time.perf_counter()
+    barrier(ws)
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), (t_host1 - t_host0) * 1e3) / args.steps, ws)
+
+    # per-kernel device times (library CUDA events on the launching stream), eager steps
+    L.profile_reset()
+    L.profile_enable(True)
+    for k in range(args.profile_steps):
+        load_batch(total_steps + k)
+        step.run()
+    prof = L.profile_read()
+    L.profile_enable(False)
+    I = int(step.rast.n_inst.item())
+    R_vis = int((step.rast.touched[:V * n] > 0).sum().item())
+    P = step.rast.total_pixels
+    bits = 32 + int(np.ceil(np.log2(max(step.rast.total_tiles, 2))))
+    passes = (bits + 7) // 8
+    per_step = {k: v[0] / args.profile_steps for k, v in prof.items()}
+    launches_per_step = sum(KERNELS_PER_SCOPE.get(k, 1) * v[1] for k, v in prof.items()) / args.profile_steps
+    launches_per_step += 1  # the Adam step-counter kernel
+    tot = sum(per_step.values())
+    dominant = max(per_step, key=per_step.get)
+    dom_launches = prof[dominant][1] / args.profile_steps
+    dom_ms = per_step[dominant] / dom_launches
+    alg = algorithmic_bytes(dominant, n, V, I, R_vis, P, passes)
+    hbm_peak, peak_kind = measured_peaks()
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+    traffic = stored_traffic(dominant)
+
+    value = ws * 1000.0 / ms_max
+    line = {
+        "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded room depth video + hidden 4D Gaussian scene; no dataset)",
+        "config": {"workload": "train_step_1M_8views", "n_gaussians": n, "n_dynamic": wl["n_dynamic"],
+                   "views": "4x960x540+4x480x270", "tile": "16x16", "loss": "L1",
+                   "graph": not args.eager, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (params 90 MB + records 430 MB + bins per step)",
+                   "instances": I, "visible_records": R_vis, "pixels": P},
+        "e2e": {"value": ws * 1000.0 / e2e_ms, "unit": "it/s",
+                "h2d_bytes_per_step": int(step.target.numel() * 4 + V * 80), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": traffic, "algorithmic_bytes": alg, "ms_per_launch": dom_ms},
+        "kernels_ms_per_step": {k: round(v, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
+        "kernel_share": {k: round(v / tot, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
+        "prune": {"ms": wl["prune_ms"], "points": N_FRAMES * VIDEO_W * VIDEO_H,
+                  "gpoints_per_s": N_FRAMES * VIDEO_W * VIDEO_H / wl["prune_ms"] / 1e6},
+        "clocks": clk,
+        "capacity_overflow": overflow,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        g, prune_s = oracle_workload(vid)
+        px = 16
+        sec = oracle_step_sample(g, *batches[0], px, 0)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "it/s", "cores": oracle.max_threads(), "kind": "oracle",
+                                "sample": f"oracle projection of all {g['mean4'].shape[0]} Gaussians + fwd+bwd of {px} "
+                                          f"random pixels in one 960x540 and one 480x270 view, extrapolated "
+                                          f"linearly to the 8-view batch; oracle pruning of the full video "
+                                          f"took {prune_s:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, ws, rank)
+        return
+    ws, rank, local = dist_init()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -248,6 +248,30 @@ I4D_API int32_t i4d_prune_points_xyz(const float* xyz, const float* rgb, const f
                              float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
                              void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * i4d_init_heuristic -- 4D Gaussians from the pruned voxels (Sec. 4.1 and Sec. 3.3
+ * "Motion-Aware Gaussian"): mean4 = (centroid, mean frame time); log-scales (log spatial_scale x3,
+ * log s_t) with s_t = st_dynamic for dynamic voxels (two frames, 2/fps in the paper) and
+ * st_static for static ones (the video length); q_l = q_r = 1 (R = I); opacity logit of
+ * `opacity`; base colour = mean colour; SH coefficients zero.
+ *   xyz (n x 3), rgb (n x 3, NULL = grey), t (n, NULL = 0.5), flag (n, NULL = static): DEVICE in
+ *   params: DEVICE out, flat layout for sh_deg
+ */
+I4D_API int32_t i4d_init_heuristic(const float* xyz, const float* rgb, const float* t, const uint8_t* flag,
+                                   int32_t n, int32_t sh_deg, float spatial_scale, float st_dynamic,
+                                   float st_static, float opacity, float* params, void* stream);
+
+/*
+ * Kernel timing (host-side tracing): when enabled, every kernel the library launches is bracketed
+ * by two CUDA events recorded on its stream; i4d_profile_read() waits for them and returns, per
+ * kernel name, the summed device time and the launch count.  Off by default; costs two event
+ * records per launch when on.  Not for use during CUDA-graph capture.
+ */
+I4D_API int32_t i4d_profile_enable(int32_t on);
+I4D_API void i4d_profile_reset(void);
+I4D_API int32_t i4d_profile_count(void);
+I4D_API int32_t i4d_profile_read(int32_t k, char* name, int32_t name_len, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

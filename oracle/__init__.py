@@ -122,8 +122,9 @@ def project(g: dict, cam: dict, tile=(16, 16), settings=None) -> np.ndarray:
     return out
 
 
-def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=None):
-    """Per-pixel depth-sorted compositing -> (img (npix,3), T_final, n_contrib, margin)."""
+def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=None, depth_margin=False):
+    """Per-pixel depth-sorted compositing -> (img (npix,3), T_final, n_contrib, margin), plus the
+    depth-order margin (smallest relative depth gap between two fragments) when depth_margin."""
     lib = _load()
     n = proj.shape[0]
     W, H = int(cam["W"]), int(cam["H"])
@@ -134,11 +135,12 @@ def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=N
     T = np.zeros(npix, dtype=np.float64)
     nc = np.zeros(npix, dtype=np.int32)
     mg = np.zeros(npix, dtype=np.float64)
+    dmg = np.zeros(npix, dtype=np.float64)
     rc = lib.orc_render(n, _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S),
-                        npix, _ptr(pix_arr), _ptr(img), _ptr(T), _ptr(nc), _ptr(mg))
+                        npix, _ptr(pix_arr), _ptr(img), _ptr(T), _ptr(nc), _ptr(mg), _ptr(dmg))
     if rc != 0:
         raise RuntimeError(f"orc_render failed ({rc})")
-    return img, T, nc, mg
+    return (img, T, nc, mg, dmg) if depth_margin else (img, T, nc, mg)
 
 
 def render_bwd(g: dict, cam: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), settings=None, pix=None):
@@ -230,3 +232,19 @@ def cov4(logscale4, ql, qr, mode: int = MODE_FULL) -> np.ndarray:
     out = np.zeros(16, dtype=np.float64)
     lib.orc_cov4(int(mode), _ptr(_f64(logscale4)), _ptr(_f64(ql)), _ptr(_f64(qr)), _ptr(out))
     return out.reshape(4, 4)
+
+
+def init_heuristic(pruned: dict, spatial_scale: float, st_dynamic: float, st_static: float = 1.0,
+                   opacity: float = 0.1) -> dict:
+    """4D Gaussians from pruned voxels (Sec. 4.1; Sec. 3.3 "Motion-Aware Gaussian"): mean = (centroid,
+    mean time); s_t = st_dynamic for dynamic voxels, st_static for static ones; isotropic spatial
+    scale; R = I; opacity logit of `opacity`; colour = mean colour."""
+    n = len(pruned["rep"])
+    mean4 = np.c_[pruned["centroid"], pruned["t"]]
+    ls = np.zeros((n, 4))
+    ls[:, :3] = np.log(spatial_scale)
+    ls[:, 3] = np.where(pruned["flag"] != 0, np.log(st_dynamic), np.log(st_static))
+    q = np.zeros((n, 4))
+    q[:, 0] = 1.0
+    return dict(mean4=mean4, logscale4=ls, ql=q, qr=q.copy(), opacity=np.full(n, np.log(opacity / (1 - opacity))),
+                rgb=pruned["rgb"], sh=np.zeros((n, 0, 3)), sh_deg=0, mode=MODE_FULL)

@@ -388,9 +388,11 @@ static int frag_cmp(const void* pa, const void* pb) {
  * Collect the fragments of pixel (px, py): every visible Gaussian whose 3-sigma ellipse covers
  * the pixel centre (q <= q_max) and whose alpha = min(alpha_max, o_t exp(-q/2)) reaches
  * alpha_min, sorted by (depth, id).  *margin collects the smallest relative distance of any
- * of these decisions from its threshold (used to explain FP32-vs-FP64 differences).
+ * of these decisions from its threshold, *dmargin the smallest relative gap between the depths of
+ * two fragments (both used to explain FP32-vs-FP64 differences).
  */
-static int gather_pixel(int n, const double* P, const double* S, int px, int py, frag* buf, double* margin) {
+static int gather_pixel(int n, const double* P, const double* S, int px, int py, frag* buf, double* margin,
+                        double* dmargin) {
   const double cxp = px + 0.5, cyp = py + 0.5;
   int cnt = 0;
   for (int i = 0; i < n; ++i) {
@@ -419,7 +421,7 @@ static int gather_pixel(int n, const double* P, const double* S, int px, int py,
   }
   qsort(buf, cnt, sizeof(frag), frag_cmp);
   for (int k = 0; k + 1 < cnt; ++k)
-    *margin = fmin(*margin, fabs(buf[k + 1].depth - buf[k].depth) / buf[k].depth);
+    *dmargin = fmin(*dmargin, fabs(buf[k + 1].depth - buf[k].depth) / buf[k].depth);
   return cnt;
 }
 
@@ -451,10 +453,10 @@ static int composite(const double* P, const double* S, const frag* buf, int cnt,
 
 /*
  * Render npix pixels (indices py*W + px; pix == NULL means all W*H in raster order) from the
- * records of orc_project.  img: npix x 3 (pixel-major), Tfinal, ncontrib, margin: npix.
+ * records of orc_project.  img: npix x 3 (pixel-major), Tfinal, ncontrib, margin, dmargin: npix.
  */
 int orc_render(int n, const double* P, const double* cam, const double* bg, const double* S, int npix,
-               const int* pix, double* img, double* Tfinal, int* ncontrib, double* margin) {
+               const int* pix, double* img, double* Tfinal, int* ncontrib, double* margin, double* dmargin) {
   const int W = (int)cam[C_W], H = (int)cam[C_H];
   if (pix == NULL && npix != W * H) return -1;
   int err = 0;
@@ -470,14 +472,15 @@ int orc_render(int n, const double* P, const double* cam, const double* bg, cons
       if (!buf) continue;
       const int p = pix ? pix[j] : j;
       const int px = p % W, py = p / W;
-      double mg = INFINITY, C[3], T;
-      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg);
+      double mg = INFINITY, dmg = INFINITY, C[3], T;
+      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg, &dmg);
       ncontrib[j] = composite(P, S, buf, cnt, bg, C, &T, &mg);
       img[3 * j + 0] = C[0];
       img[3 * j + 1] = C[1];
       img[3 * j + 2] = C[2];
       Tfinal[j] = T;
       margin[j] = mg;
+      dmargin[j] = dmg;
     }
     free(buf);
   }
@@ -738,8 +741,8 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
       const int px = p % W, py = p / W;
       const double* gC = dL_dimg + 3 * (size_t)j;
       if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
-      double mg = INFINITY, C[3], T;
-      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg);
+      double mg = INFINITY, dmg = INFINITY, C[3], T;
+      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg, &dmg);
       const int nb = composite(P, S, buf, cnt, bg, C, &T, &mg);
       pixel_backward(P, buf, nb, T, bg, gC, px, py, S, Tb, g2);
     }

@@ -83,6 +83,12 @@ _SIGS = {
                                  c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "i4d_prune_points_xyz": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f, c_f, c_i32, c_i64, c_i64, c_vp, c_vp, c_vp,
                                      c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "i4d_init_heuristic": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_f, c_f, c_f, c_f, c_vp, c_vp]),
+    "i4d_profile_enable": (c_i32, [c_i32]),
+    "i4d_profile_reset": (None, []),
+    "i4d_profile_count": (c_i32, []),
+    "i4d_profile_read": (c_i32, [c_i32, ctypes.c_char_p, c_i32, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(c_i64)]),
 }
 
 
@@ -216,3 +222,32 @@ def i4d_prune_points_xyz(xyz, rgb, t, dyn, voxel_static, voxel_dynamic, min_supp
                                       ptr(rep), ptr(count), ptr(xyz_out), ptr(rgb_out), ptr(t_out), ptr(flag),
                                       ptr(n_kept), ptr(status), ptr(ws), ws.numel() * ws.element_size(),
                                       stream_ptr(stream)), "i4d_prune_points_xyz")
+
+
+def i4d_init_heuristic(xyz, rgb, t, flag, n, sh_deg, spatial_scale, st_dynamic, st_static, opacity, params,
+                       stream=None):
+    check(load().i4d_init_heuristic(ptr(xyz), ptr(rgb), ptr(t), ptr(flag), int(n), int(sh_deg), float(spatial_scale),
+                                    float(st_dynamic), float(st_static), float(opacity), ptr(params),
+                                    stream_ptr(stream)), "i4d_init_heuristic")
+
+
+def profile_enable(on: bool = True) -> None:
+    load().i4d_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    load().i4d_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} of the launches recorded since the last reset (syncs)."""
+    lib = load()
+    out = {}
+    for k in range(lib.i4d_profile_count()):
+        name = ctypes.create_string_buffer(64)
+        ms = ctypes.c_double()
+        cnt = c_i64()
+        check(lib.i4d_profile_read(k, name, 64, ctypes.byref(ms), ctypes.byref(cnt)), "i4d_profile_read")
+        if cnt.value:
+            out[name.value.decode()] = (ms.value, int(cnt.value))
+    return out

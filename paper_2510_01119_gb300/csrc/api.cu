@@ -247,6 +247,17 @@ int32_t i4d_adam_step(float* params, const float* grads, float* m, float* v, int
   return cuda_status(launch_adam(params, grads, m, v, count, G, step, beta1, beta2, eps, (cudaStream_t)stream));
 }
 
+int32_t i4d_init_heuristic(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int32_t n,
+                           int32_t sh_deg, float spatial_scale, float st_dynamic, float st_static, float opacity,
+                           float* params, void* stream) {
+  if (n < 0 || sh_deg < 0 || sh_deg > 3 || !(spatial_scale > 0.0f) || !(st_dynamic > 0.0f) || !(st_static > 0.0f) ||
+      !(opacity > 0.0f && opacity < 1.0f))
+    return I4D_ERR_ARG;
+  if (n > 0 && (!xyz || !params || !aligned16(params))) return I4D_ERR_ARG;
+  return cuda_status(launch_init_heuristic(xyz, rgb, t, flag, n, sh_deg, spatial_scale, st_dynamic, st_static,
+                                           opacity, params, (cudaStream_t)stream));
+}
+
 size_t i4d_prune_workspace_size(int64_t n_points, int64_t table_slots) {
   if (n_points < 0 || table_slots < 1 || (table_slots & (table_slots - 1))) return 0;
   return prune_workspace_bytes(n_points, table_slots);
@@ -280,7 +291,7 @@ int32_t i4d_prune_points(const float* depth, const uint8_t* rgb, const uint8_t* 
                          int32_t min_support, int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count,
                          float* xyz, float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
                          void* ws, size_t ws_bytes, void* stream) {
-  if (F < 0 || W < 0 || H < 0 || !depth || !cams) return I4D_ERR_ARG;
+  if (F < 0 || F > 65535 || W < 0 || H < 0 || !depth || !cams) return I4D_ERR_ARG;
   const int64_t np = (int64_t)F * W * H;
   return prune_common(depth, rgb, dyn, cams, F, W, H, nullptr, nullptr, nullptr, np, voxel_static, voxel_dynamic,
                       min_support, table_slots, capacity, rep, count, xyz, rgb_out, t_out, flag, n_kept, status, ws,

@@ -258,6 +258,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_
     if (total) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
     return cudaSuccess;
   }
+  I4D_PROF("scan", st);
   scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, chunk, bsum);
   scan_top_kernel<<<1, kScanThreads, 0, st>>>(bsum, nb, total);
   scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n, chunk, bsum);
@@ -290,9 +291,13 @@ cudaError_t launch_radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt
     const uint32_t* vin = (p == 0) ? vals : vb[p & 1];
     uint64_t* kout = kb[(p + 1) & 1];
     uint32_t* vout = (p == passes - 1) ? vals_out : vb[(p + 1) & 1];
-    radix_hist_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, n_dev, capacity, 8 * p, nblocks, hist);
+    {
+      I4D_PROF("radix_hist", st);
+      radix_hist_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, n_dev, capacity, 8 * p, nblocks, hist);
+    }
     cudaError_t e = launch_scan_u32(hist, hist, hist_n, nullptr, scan_ws, st);
     if (e != cudaSuccess) return e;
+    I4D_PROF("radix_scatter", st);
     radix_scatter_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, capacity, 8 * p, nblocks, hist);
   }
   if (keys_result) *keys_result = kb[passes & 1];
@@ -304,6 +309,7 @@ cudaError_t launch_emit_keys(const ViewTable& vt, int n, const float* proj, cons
                              cudaStream_t st) {
   const int64_t VN = (int64_t)vt.n_views * n;
   if (VN == 0) return cudaSuccess;
+  I4D_PROF("emit_keys", st);
   const int threads = 256;
   const int64_t blocks = (VN + threads - 1) / threads;
   emit_keys_kernel<<<(unsigned)blocks, threads, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), touched,
@@ -315,6 +321,7 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64
                                int64_t total_tiles, int32_t* status, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, st);
   if (e != cudaSuccess) return e;
+  I4D_PROF("tile_ranges", st);
   const int threads = 256;
   const int64_t blocks = (capacity + threads - 1) / threads;
   tile_ranges_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, st>>>(keys, n_dev, capacity, ranges, status);

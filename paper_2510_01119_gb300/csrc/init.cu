@@ -1,0 +1,45 @@
+// Heuristic initialisation of 4D Gaussians from the pruned voxels (Sec. 4.1, Sec. 3.3
+// "Motion-Aware Gaussian"): mean = (centroid, averaged frame time); temporal scale s_t = two
+// frames for dynamic voxels and the whole video for static ones; isotropic spatial scale;
+// identity rotation (R = I); averaged colour; one opacity for all.
+#include "kernels.cuh"
+#include "profile.cuh"
+
+namespace i4d {
+
+namespace {
+
+__global__ void __launch_bounds__(256) init_heuristic_kernel(const float* __restrict__ xyz,
+                                                             const float* __restrict__ rgb,
+                                                             const float* __restrict__ t,
+                                                             const uint8_t* __restrict__ flag, int n, int nplanes,
+                                                             float log_s, float log_st_dyn, float log_st_static,
+                                                             float opac_logit, float4* __restrict__ P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t N = (size_t)n;
+  const bool dyn = flag ? (flag[i] != 0) : false;
+  P[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], t ? t[i] : 0.5f);
+  P[N + i] = make_float4(log_s, log_s, log_s, dyn ? log_st_dyn : log_st_static);
+  P[2 * N + i] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+  P[3 * N + i] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+  P[4 * N + i] = make_float4(opac_logit, rgb ? rgb[3 * i] : 0.5f, rgb ? rgb[3 * i + 1] : 0.5f,
+                             rgb ? rgb[3 * i + 2] : 0.5f);
+  for (int p = 5; p < nplanes; ++p) P[(size_t)p * N + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+}  // namespace
+
+cudaError_t launch_init_heuristic(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int n,
+                                  int sh_deg, float spatial_scale, float st_dynamic, float st_static, float opacity,
+                                  float* params, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  I4D_PROF("init_heuristic", st);
+  const float opac_logit = logf(opacity / (1.0f - opacity));
+  init_heuristic_kernel<<<(n + 255) / 256, 256, 0, st>>>(xyz, rgb, t, flag, n, 5 + sh_planes(sh_deg),
+                                                          logf(spatial_scale), logf(st_dynamic), logf(st_static),
+                                                          opac_logit, reinterpret_cast<float4*>(params));
+  return cudaGetLastError();
+}
+
+}  // namespace i4d

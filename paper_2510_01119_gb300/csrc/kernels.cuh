@@ -2,6 +2,7 @@
 #pragma once
 
 #include "i4d_common.cuh"
+#include "profile.cuh"
 
 namespace i4d {
 
@@ -64,5 +65,9 @@ cudaError_t launch_prune(const float* depth, const uint8_t* rgb8, const uint8_t*
                          int W, int H, const float* xyz, const float* rgbf, const float* tpt, int64_t n_points,
                          float inv_static, float inv_dynamic, int min_support, int64_t table_slots, int64_t capacity,
                          const PruneOut& out, void* ws, cudaStream_t st);
+
+cudaError_t launch_init_heuristic(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int n,
+                                  int sh_deg, float spatial_scale, float st_dynamic, float st_static, float opacity,
+                                  float* params, cudaStream_t st);
 
 }  // namespace i4d

@@ -116,6 +116,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
                         int32_t* step, float b1, float b2, float eps, cudaStream_t st) {
   const int64_t n4 = count / 4;
   if (n4 > 0) {
+    I4D_PROF("adam", st);
     int64_t blocks = (n4 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
@@ -130,6 +131,7 @@ cudaError_t launch_loss(const float* img, const float* target, int64_t count, in
                         float* loss_out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), st);
   if (e != cudaSuccess || count == 0) return e;
+  I4D_PROF("loss", st);
   loss_kernel<<<reduce_blocks(count), 256, 0, st>>>(img, target, count, kind, 1.0f / (float)count, dL_dimg, loss_out);
   return cudaGetLastError();
 }

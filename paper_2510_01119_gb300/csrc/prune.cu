@@ -44,8 +44,9 @@ __device__ __forceinline__ int64_t voxel_coord(float x, float inv) { return (int
 
 __device__ __forceinline__ bool make_key(float x, float y, float z, int flag, float inv, uint64_t& key) {
   const int64_t ix = voxel_coord(x, inv), iy = voxel_coord(y, inv), iz = voxel_coord(z, inv);
+  // (iz stops one short of the top so that no key can equal the all-ones empty marker)
   if (ix < -kCoordHalf || ix >= kCoordHalf || iy < -kCoordHalf || iy >= kCoordHalf || iz < -kCoordHalf ||
-      iz >= kCoordHalf)
+      iz >= kCoordHalf - 1)
     return false;
   const uint64_t m = (1ull << kCoordBits) - 1;
   key = ((uint64_t)flag << 63) | ((uint64_t)(ix + kCoordHalf) & m) << 42 | ((uint64_t)(iy + kCoordHalf) & m) << 21 |
@@ -298,26 +299,38 @@ cudaError_t launch_prune(const float* depth, const uint8_t* rgb8, const uint8_t*
   PruneWs w = carve(ws, table_slots, cap_int);
   const int threads = 256;
   const int64_t sblocks = (table_slots + threads - 1) / threads;
-  table_init_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T);
+  {
+    I4D_PROF("prune_table_init", st);
+    table_init_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T);
+  }
   if (depth) {
+    I4D_PROF("prune_insert", st);
     const int tiles_x = (W + 31) / 32, tiles_y = (H + 7) / 8;
     dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)F);
     if (F > 0 && W > 0 && H > 0)
       insert_depth_kernel<<<grid, threads, 0, st>>>(depth, rgb8, dyn, cams, W, H, tiles_x, inv_static, inv_dynamic,
                                                     w.T, out.status);
   } else if (n_points > 0) {
+    I4D_PROF("prune_insert", st);
     const int64_t blocks = (n_points + threads - 1) / threads;
     insert_xyz_kernel<<<(unsigned)blocks, threads, 0, st>>>(xyz, rgbf, tpt, dyn, n_points, inv_static, inv_dynamic,
                                                            w.T, out.status);
   }
-  table_flags_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T, min_support, w.flags);
+  {
+    I4D_PROF("prune_compact", st);
+    table_flags_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T, min_support, w.flags);
+  }
   cudaError_t e = launch_scan_u32(w.flags, w.offs, table_slots, w.total, w.scan_ws, st);
   if (e != cudaSuccess) return e;
-  table_compact_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T, w.flags, w.offs, cap_int, w.sk[0], w.sv[0]);
+  {
+    I4D_PROF("prune_compact", st);
+    table_compact_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T, w.flags, w.offs, cap_int, w.sk[0], w.sv[0]);
+  }
   e = launch_radix_sort(w.sk[0], w.sv[0], w.sk[1], w.sv[1], w.sorted_slots, cap_int, w.total, 32, w.radix_ws,
                         nullptr, st);
   if (e != cudaSuccess) return e;
   const int64_t oblocks = (capacity + threads - 1) / threads;
+  I4D_PROF("prune_gather", st);
   gather_kernel<<<(unsigned)(oblocks > 0 ? oblocks : 1), threads, 0, st>>>(w.T, w.sorted_slots, w.total, capacity,
                                                                             out);
   return cudaGetLastError();

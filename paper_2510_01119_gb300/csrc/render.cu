@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(ViewTable vt, int n
   const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
   if ((threadIdx.x & 31) == 0) atomicMax(&smax, wmax);
   __syncthreads();
-  const uint32_t end = rg.x + smax;
+  const uint32_t end = rg.x + min(smax, rg.y - rg.x);  // never past the tile's range
   for (uint32_t hi = end; hi > rg.x;) {
     const uint32_t lo = (hi - rg.x > (uint32_t)B) ? hi - B : rg.x;
     __syncthreads();
@@ -217,6 +217,7 @@ cudaError_t launch_fwd_t(const ViewTable& vt, int n, const float* proj, const ui
                          const Settings& S, float* img, float* T_final, uint32_t* last, uint32_t* n_contrib,
                          cudaStream_t st) {
   const int tiles = vt.tile_off[vt.n_views];
+  I4D_PROF("render_fwd", st);
   render_fwd_kernel<TW, TH><<<tiles, TW * TH, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
                                                         reinterpret_cast<const uint2*>(ranges), S, img, T_final, last,
                                                         n_contrib);
@@ -228,6 +229,7 @@ cudaError_t launch_bwd_t(const ViewTable& vt, int n, const float* proj, const ui
                          const Settings& S, const float* T_final, const uint32_t* last, const float* dL_dimg,
                          float* grad2d, cudaStream_t st) {
   const int tiles = vt.tile_off[vt.n_views];
+  I4D_PROF("render_bwd", st);
   render_bwd_kernel<TW, TH><<<tiles, TW * TH, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
                                                         reinterpret_cast<const uint2*>(ranges), S, T_final, last,
                                                         dL_dimg, reinterpret_cast<float4*>(grad2d));
@@ -258,7 +260,11 @@ cudaError_t launch_render_bwd(const ViewTable& vt, int n, const float* proj, con
                               const uint32_t* ranges, const Settings& S, const float* T_final, const uint32_t* last,
                               const float* dL_dimg, float* grad2d, cudaStream_t st) {
   const size_t VN = (size_t)vt.n_views * n;
-  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float) * I4D_GRAD2D_FLOATS * VN, st);
+  cudaError_t e;
+  {
+    I4D_PROF("grad2d_clear", st);
+    e = cudaMemsetAsync(grad2d, 0, sizeof(float) * I4D_GRAD2D_FLOATS * VN, st);
+  }
   if (e != cudaSuccess) return e;
   if (vt.tile_off[vt.n_views] == 0) return cudaSuccess;
   I4D_TILE_DISPATCH(launch_bwd_t, vt, n, proj, ids, ranges, S, T_final, last, dL_dimg, grad2d, st);

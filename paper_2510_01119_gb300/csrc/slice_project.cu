@@ -120,6 +120,7 @@ cudaError_t launch_slice_project(const float* params, int n, int sh_deg, int mod
                                  const i4d_camera* cams, const Settings& S, float* proj, uint32_t* touched,
                                  cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  I4D_PROF("slice_project", st);
   const int threads = 256, blocks = (n + threads - 1) / threads;
   const float4* P = reinterpret_cast<const float4*>(params);
   float4* R = reinterpret_cast<float4*>(proj);
@@ -136,6 +137,7 @@ cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int
                                      const i4d_camera* cams, const Settings& S, const uint32_t* touched,
                                      const float* grad2d, float* grads, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  I4D_PROF("slice_project_bwd", st);
   const int threads = 128, blocks = (n + threads - 1) / threads;
   const float4* P = reinterpret_cast<const float4*>(params);
   const float4* G2 = reinterpret_cast<const float4*>(grad2d);

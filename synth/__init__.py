@@ -190,19 +190,102 @@ def subset(g: dict, idx) -> dict:
 # ------------------------------------------------------------------------------------------
 # depth-map video (ray-cast analytic room with moving spheres)
 # ------------------------------------------------------------------------------------------
-ROOM = dict(x=(-2.9, 2.9), y=(-1.6, 1.6), z_back=6.5)   # side walls, floor (+y) / ceiling, back wall
+# side walls, floor (+y) / ceiling, back wall; extents chosen so that pruning the 200-frame
+# 640x360 video at a 0.01 voxel with minimum support 3 keeps about one million voxels
+PRUNE_VOXEL = 0.01
+PRUNE_MIN_SUPPORT = 3
+ROOM = dict(x=(-0.812, 0.812), y=(-0.448, 0.448), z_back=3.98)
+
+
+def room_colour(p: np.ndarray, kind: np.ndarray) -> np.ndarray:
+    """Procedural texture of the room: colour of world point p on surface `kind` (1-5 planes,
+    10+ spheres), in [0, 1]."""
+    tex = 0.5 + 0.25 * np.sin(7.0 * p[..., 0]) * np.cos(5.0 * p[..., 1]) + 0.25 * np.sin(3.0 * p[..., 2])
+    base = np.stack([0.3 + 0.1 * (kind % 3), 0.4 + 0.1 * (kind % 2), 0.5 + 0.05 * (kind % 5)], -1)
+    return np.clip(base * (0.5 + tex[..., None]), 0.0, 1.0)
+
+
+def room_spheres(seed: int, room: dict = None):
+    """(centres at t = 0.5, radii, velocities) of the three moving spheres of the room video."""
+    room = ROOM if room is None else room
+    r = rng(seed)
+    sx, sy, sz = 0.4 * room["x"][1], 0.4 * room["y"][1], room["z_back"]
+    c0 = np.stack([r.uniform(-sx, sx, 3), r.uniform(-sy, sy, 3), r.uniform(0.45 * sz, 0.75 * sz, 3)], axis=1)
+    rad = r.uniform(0.3, 0.5, 3) * (sz / 6.5)
+    vel = r.normal(0.0, 0.3, size=(3, 3))
+    return c0, rad, vel, r
+
+
+def room_gaussians(seed: int = 1003, n: int = 200000, video_seed: int = 2, dyn_frac: float = 0.1,
+                   n_frames: int = 200, room: dict = None) -> dict:
+    """Hidden 4D Gaussian scene of the room video: static Gaussians on the planes seen by the arc
+    cameras (temporal scale of the whole video) and dynamic Gaussians on the three moving spheres of
+    the video with seed `video_seed` (velocity encoded in the 4D rotation, temporal scale of a few
+    frames), coloured by the room texture; SH degree 0, isotropic spatial scale."""
+    room = ROOM if room is None else room
+    r = rng(seed)
+    n_dyn = int(n * dyn_frac)
+    n_st = n - n_dyn
+    x0, x1 = room["x"]
+    y0, y1 = room["y"]
+    zb = room["z_back"]
+    zlo = 0.8
+    # planes with their areas inside the visible box
+    planes = [(5, "z", zb, (x0, x1), (y0, y1)), (1, "x", x0, (y0, y1), (zlo, zb)), (2, "x", x1, (y0, y1), (zlo, zb)),
+              (3, "y", y1, (x0, x1), (zlo, zb)), (4, "y", y0, (x0, x1), (zlo, zb))]
+    areas = np.array([(a[1] - a[0]) * (b[1] - b[0]) for (_, _, _, a, b) in planes])
+    which = r.choice(len(planes), size=n_st, p=areas / areas.sum())
+    pts = np.zeros((n_st, 3))
+    kind = np.zeros(n_st, np.int64)
+    for k, (kd, ax, val, ra, rb) in enumerate(planes):
+        m = which == k
+        u = r.uniform(ra[0], ra[1], m.sum())
+        v = r.uniform(rb[0], rb[1], m.sum())
+        if ax == "z":
+            pts[m] = np.c_[u, v, np.full(m.sum(), val)]
+        elif ax == "x":
+            pts[m] = np.c_[np.full(m.sum(), val), u, v]
+        else:
+            pts[m] = np.c_[u, np.full(m.sum(), val), v]
+        kind[m] = kd
+    c0, rad, vel, _ = room_spheres(video_seed, room)
+    sph = r.integers(0, 3, n_dyn)
+    d = r.normal(size=(n_dyn, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t_dyn = r.uniform(0.0, 1.0, n_dyn)
+    dyn_pts = c0[sph] + rad[sph, None] * d + vel[sph] * (t_dyn[:, None] - 0.5)
+    mean4 = np.zeros((n, 4), np.float32)
+    mean4[:n_st, :3] = pts
+    mean4[:n_st, 3] = 0.5
+    mean4[n_st:, :3] = dyn_pts
+    mean4[n_st:, 3] = t_dyn
+    ls = np.zeros((n, 4), np.float32)
+    spacing = math.sqrt(areas.sum() / max(n_st, 1))
+    ls[:n_st, :3] = math.log(0.6 * spacing)
+    ls[:n_st, 3] = math.log(1.0)
+    s_dyn = 0.6 * math.sqrt(4 * math.pi * float(np.mean(rad ** 2)) / max(n_dyn / 3, 1)) * 3
+    ls[n_st:, :3] = math.log(s_dyn)
+    ls[n_st:, 3] = math.log(3.0 / max(n_frames - 1, 1))
+    ql = np.zeros((n, 4), np.float32)
+    ql[:, 0] = 1.0
+    qr = ql.copy()
+    qv_l, qv_r = velocity_quats(vel[sph], np.full(n_dyn, s_dyn), np.full(n_dyn, 3.0 / max(n_frames - 1, 1)))
+    ql[n_st:], qr[n_st:] = qv_l, qv_r
+    rgb = np.zeros((n, 3), np.float32)
+    rgb[:n_st] = room_colour(pts, kind)
+    rgb[n_st:] = room_colour(dyn_pts, 10 + sph)
+    return dict(mean4=mean4, logscale4=ls, ql=ql, qr=qr, opacity=np.full(n, 2.0, np.float32), rgb=rgb,
+                sh=np.zeros((n, 0, 3), np.float32), sh_deg=0, mode=MODE_FULL)
 
 
 def depth_video(seed: int = 2, n_frames: int = 200, W: int = 640, H: int = 360, frames=None,
-                noise: float = 0.01, fov_x_deg: float = 60.0):
+                noise: float = 0.01, fov_x_deg: float = 60.0, room: dict = None):
     """Depth maps of a room (floor, back wall, two side walls; z-depth clipped to [1, 10] m) with
     3 spheres moving linearly, seen from the arc camera, with multiplicative depth noise
     (1 + noise N(0,1)).  Returns dict(depth (F,H,W) f32, rgb (F,H,W,3) u8, dyn (F,H,W) u8, cams,
     times).  `frames` selects a subset of frame indices (same values as in the full video)."""
-    r = rng(seed)
-    sph_c0 = np.stack([r.uniform(-1.2, 1.2, 3), r.uniform(-0.6, 0.6, 3), r.uniform(3.0, 5.0, 3)], axis=1)
-    sph_r = r.uniform(0.3, 0.5, 3)
-    sph_v = r.normal(0.0, 0.3, size=(3, 3))
+    room = ROOM if room is None else room
+    sph_c0, sph_r, sph_v, r = room_spheres(seed, room)
     frames = list(range(n_frames)) if frames is None else list(frames)
     F = len(frames)
     depth = np.zeros((F, H, W), np.float32)
@@ -220,8 +303,8 @@ def depth_video(seed: int = 2, n_frames: int = 200, W: int = 640, H: int = 360, 
         dw = dc @ R                       # world ray directions, scaled so that camera z = 1
         best = np.full((H, W), np.inf)
         hit_kind = np.zeros((H, W), np.int32)
-        for axis, val, kind in ((0, ROOM["x"][0], 1), (0, ROOM["x"][1], 2), (1, ROOM["y"][1], 3),
-                                (1, ROOM["y"][0], 4), (2, ROOM["z_back"], 5)):
+        for axis, val, kind in ((0, room["x"][0], 1), (0, room["x"][1], 2), (1, room["y"][1], 3),
+                                (1, room["y"][0], 4), (2, room["z_back"], 5)):
             with np.errstate(divide="ignore", invalid="ignore"):
                 s = (val - eye[axis]) / dw[..., axis]
             ok = (s > 0) & (s < best)
@@ -244,10 +327,7 @@ def depth_video(seed: int = 2, n_frames: int = 200, W: int = 640, H: int = 360, 
         d = d * (1.0 + noise * r.normal(size=d.shape))
         depth[fi] = d.astype(np.float32)
         hit = eye + best[..., None] * dw
-        tex = 0.5 + 0.25 * np.sin(7.0 * hit[..., 0]) * np.cos(5.0 * hit[..., 1]) + 0.25 * np.sin(3.0 * hit[..., 2])
-        base = np.stack([0.3 + 0.1 * (hit_kind % 3), 0.4 + 0.1 * (hit_kind % 2), 0.5 + 0.05 * (hit_kind % 5)], -1)
-        col = np.clip(base * (0.5 + tex[..., None]), 0.0, 1.0)
-        rgb[fi] = (col * 255.0 + 0.5).astype(np.uint8)
+        rgb[fi] = (room_colour(hit, hit_kind) * 255.0 + 0.5).astype(np.uint8)
         dyn[fi] = (hit_kind >= 10).astype(np.uint8)
     times = np.array([k / max(n_frames - 1, 1) for k in frames], np.float32)
     return dict(depth=depth, rgb=rgb, dyn=dyn, cams=cams, times=times)

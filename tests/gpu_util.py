@@ -5,6 +5,9 @@ import numpy as np
 # order) sit within this relative margin of a threshold may legitimately differ between the FP32
 # GPU and the FP64 oracle; every other pixel must match to IMG_TOL.
 FLAG_MARGIN = 1e-4
+# Two fragments whose depths differ by less than this relative gap may swap order (FP32 depth is
+# good to ~1e-7 relative).
+DEPTH_MARGIN = 1e-5
 IMG_TOL = 1e-4        # max-abs on rendered images
 GRAD_TOL = 1e-3       # relative L2 on gradients
 
@@ -21,9 +24,11 @@ def oracle_views(orc, g, cams, tile=(16, 16), settings=None, bg=(0, 0, 0)):
     out = []
     for cam in cams:
         P = orc.project(g, cam, tile=tile, settings=settings)
-        img, T, nc, mg = orc.render(P, cam, bg=bg, settings=settings)
+        img, T, nc, mg, dmg = orc.render(P, cam, bg=bg, settings=settings, depth_margin=True)
         W, H = int(cam["W"]), int(cam["H"])
-        out.append((P, img.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), mg.reshape(H, W)))
+        # one flag value per pixel: below FLAG_MARGIN means "may differ"
+        flag = np.minimum(mg, dmg * (FLAG_MARGIN / DEPTH_MARGIN))
+        out.append((P, img.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), flag.reshape(H, W)))
     return out
 
 
@@ -62,7 +67,7 @@ def suspicious_gaussians(orc, views_P):
         d = P[vis, C["depth"]]
         order = np.argsort(d, kind="stable")
         ds = d[order]
-        close = np.nonzero(np.diff(ds) / ds[:-1] < FLAG_MARGIN)[0] if len(ds) > 1 else []
+        close = np.nonzero(np.diff(ds) / ds[:-1] < DEPTH_MARGIN)[0] if len(ds) > 1 else []
         for k in close:
             s.add(int(vis[order[k]]))
             s.add(int(vis[order[k + 1]]))

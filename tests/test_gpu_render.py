@@ -126,7 +126,7 @@ def test_render_forward_matches_oracle(dev, orc, mode, deg):
     gimg = [x.cpu().numpy() for x in rast.split_images()]
     bad, flagged, worst = compare_images(gimg, ov)
     assert bad == 0, (bad, flagged, worst)
-    assert flagged < 0.03 * 128 * 96
+    assert flagged < 0.08 * 128 * 96
     T = rast.split_pixels(rast.T_final)[0].cpu().numpy()
     nc = rast.split_pixels(rast.n_contrib)[0].cpu().numpy()
     fl = ov[0][4] < FLAG_MARGIN
