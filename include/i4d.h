@@ -198,6 +198,23 @@ I4D_API int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, c
                        const float* dL_dimg, float* grad2d, float* grads, void* stream);
 
 /*
+ * i4d_render_bwd_noalloc -- i4d_render_bwd for callers that may not allocate device memory when they
+ * run the backward (a C/C++ host whose device heap belongs to its own memory manager, or a real-time
+ * loop that must not stall on cudaMalloc).  The paper has no counterpart: this is a deployment
+ * variant of the same computation.  The 2D-gradient scratch is a fixed array inside the library
+ * (i4d_render_bwd_noalloc_max_records() records of 48 bytes, 24 MiB, held by every GPU that loads
+ * the library until exit) instead of the grad2d argument; all other arguments are as for
+ * i4d_render_bwd.  Returns I4D_ERR_CAPACITY, launching nothing, when n_views * n exceeds the maximum.
+ * Every call shares the array: calls that overlap on the GPU race.  The first call on a device looks
+ * up the array's address with that device current; make it before any stream capture.
+ */
+I4D_API int64_t i4d_render_bwd_noalloc_max_records(void);
+I4D_API int32_t i4d_render_bwd_noalloc(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,
+                                       const i4d_settings* settings, const float* proj, const uint32_t* touched,
+                                       const uint32_t* ids, const uint32_t* ranges, const float* T_final,
+                                       const uint32_t* last, const float* dL_dimg, float* grads, void* stream);
+
+/*
  * i4d_loss -- the single photometric loss of the method (supplementary "Discussion with previous
  * work": one photometric term; Sec. 4.1: the standard 3DGS loss), L1 or MSE over every pixel and
  * channel of all views, mean-reduced; writes dL/dimg and the loss value.

@@ -84,6 +84,10 @@ _SIGS = {
     "i4d_prune_points_xyz": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f, c_f, c_i32, c_i64, c_i64, c_vp, c_vp, c_vp,
                                      c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "i4d_init_heuristic": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_f, c_f, c_f, c_f, c_vp, c_vp]),
+    "i4d_render_bwd_noalloc_max_records": (c_i64, []),
+    "i4d_render_bwd_noalloc": (c_i32, [ctypes.POINTER(Gaussians), ctypes.POINTER(Views), c_vp,
+                                       ctypes.POINTER(Settings), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                       c_vp]),
     "i4d_profile_enable": (c_i32, [c_i32]),
     "i4d_profile_reset": (None, []),
     "i4d_profile_count": (c_i32, []),
@@ -251,3 +255,16 @@ def profile_read() -> dict:
         if cnt.value:
             out[name.value.decode()] = (ms.value, int(cnt.value))
     return out
+
+
+def i4d_render_bwd_noalloc(g: Gaussians, views: Views, cams, settings, proj, touched, ids, ranges, T_final, last,
+                           dL_dimg, grads, stream=None):
+    """i4d_render_bwd without a scratch argument (the library's fixed scratch array is used)."""
+    lib = load()
+    rc = lib.i4d_render_bwd_noalloc(ctypes.byref(g), ctypes.byref(views), ptr(cams), ctypes.byref(settings),
+                                    ptr(proj), ptr(touched), ptr(ids), ptr(ranges), ptr(T_final), ptr(last),
+                                    ptr(dL_dimg), ptr(grads), stream_ptr(stream))
+    if rc == -2:
+        raise I4DError(f"i4d_render_bwd_noalloc: n_views * n = {views.n_views * g.n} exceeds the fixed scratch of "
+                       f"{int(lib.i4d_render_bwd_noalloc_max_records())} records")
+    check(rc, "i4d_render_bwd_noalloc")
