@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--eager", action="store_true", help="launch the step eagerly instead of a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--small", action="store_true",
+                    help="50-frame video (~0.4 M Gaussians) for profiler captures; not a bench value")
     return ap.parse_args()
 
 
@@ -131,9 +133,10 @@ class Clocks:
 # ------------------------------------------------------------------------------------------------
 # workload
 # ------------------------------------------------------------------------------------------------
-def make_video():
+def make_video(small: bool = False):
     import synth
-    return synth.depth_video(2, n_frames=N_FRAMES, W=VIDEO_W, H=VIDEO_H)
+    frames = list(range(0, N_FRAMES, 4)) if small else None
+    return synth.depth_video(2, n_frames=N_FRAMES, W=VIDEO_W, H=VIDEO_H, frames=frames)
 
 
 def step_batches(n_steps: int, seed: int = 3):
@@ -161,6 +164,7 @@ def build_gpu_workload(dev, vid):
     dyn = torch.from_numpy(vid["dyn"]).to(dev)
     cams = R.cameras_tensor(vid["cams"], dev)
     pr = Pruner(F * VIDEO_W * VIDEO_H, 1 << 22, capacity=1 << 22, device=dev)
+    points = F * VIDEO_W * VIDEO_H
     prune_ms = []
     for _ in range(3):  # first run warms up; report the best of the rest
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -197,7 +201,7 @@ def build_gpu_workload(dev, vid):
     cam_bank = {size: R.cameras_tensor([synth.arc_camera(k, N_FRAMES, size[0], size[1]) for k in range(N_FRAMES)],
                                        dev) for size in (FULL, HALF)}
     return dict(n=n, params=params, prune_ms=min(prune_ms[1:]), bank=bank, cam_bank=cam_bank,
-                n_dynamic=int(out["flag"][:n].sum().item()))
+                n_dynamic=int(out["flag"][:n].sum().item()), points=points)
 
 
 def algorithmic_bytes(kernel: str, n: int, V: int, I: int, R_vis: int, P: int, passes: int) -> float:
@@ -352,7 +356,7 @@ def run_ours(args, ws, rank, local):
     L.load()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    vid = make_video()
+    vid = make_video(args.small)
     wl = build_gpu_workload(dev, vid)
     n = wl["n"]
     sizes = T.sizes_for_batch(FULL, HALF, N_FULL, N_HALF)
@@ -396,11 +400,13 @@ def run_ours(args, ws, rank, local):
     clocks = Clocks(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")
     ev0.record()
     for k in range(args.steps):
         load_batch(args.warmup + k)
         run()
     ev1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
@@ -476,12 +482,14 @@ def run_ours(args, ws, rank, local):
                      "traffic": traffic, "algorithmic_bytes": alg, "ms_per_launch": dom_ms},
         "kernels_ms_per_step": {k: round(v, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
         "kernel_share": {k: round(v / tot, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
-        "prune": {"ms": wl["prune_ms"], "points": N_FRAMES * VIDEO_W * VIDEO_H,
-                  "gpoints_per_s": N_FRAMES * VIDEO_W * VIDEO_H / wl["prune_ms"] / 1e6},
+        "prune": {"ms": wl["prune_ms"], "points": wl["points"],
+                  "gpoints_per_s": wl["points"] / wl["prune_ms"] / 1e6},
         "clocks": clk,
         "capacity_overflow": overflow,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if args.small:
+        line["config"]["workload"] = "train_step_small_profile_only"
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.small:
         import oracle
         oracle.build()
         g, prune_s = oracle_workload(vid)
