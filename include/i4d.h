@@ -31,8 +31,9 @@
  *              Gaussian's SH group, i.e. plane 5 + (3k + c) / 4, lane (3k + c) % 4.
  *   A 4-vector (x, y, z, t) is the quaternion t + xi + yj + zk; R v = q_l v q_r (normalised q).
  *   Gradients use the same flat layout.
- *   Projected records: 3 planes of V x N float4 (view-major within a plane): plane 0 (u, v,
- *   conic_a, conic_b), plane 1 (conic_c, o_t, r, g), plane 2 (b, depth, radius, 0).
+ *   Projected records: 4 planes of V x N float4 (view-major within a plane): plane 0 (u, v,
+ *   conic_a, conic_b), plane 1 (conic_c, o_t, r, g), plane 2 (b, depth, radius, 0), plane 3 the
+ *   pixel-space box (xmin, xmax, ymin, ymax) of the q <= q_max ellipse, widened by 1% + 0.01 px.
  *   2D gradients (scratch of the backward): 3 planes of V x N float4: (du, dv, dconic_a,
  *   dconic_b), (dconic_c, do_t, dr, dg), (db, 0, 0, 0).
  *   Images: per view, planar float32 [3][H][W]; views concatenated in order.  Per-pixel
@@ -63,7 +64,7 @@ extern "C" {
 #define I4D_ERR_WORKSPACE (-4) /* workspace smaller than *_workspace_size() */
 
 #define I4D_MAX_VIEWS 64
-#define I4D_PROJ_FLOATS 12     /* floats per projected record (3 float4 planes) */
+#define I4D_PROJ_FLOATS 16     /* floats per projected record (4 float4 planes) */
 #define I4D_GRAD2D_FLOATS 12   /* floats per (view, Gaussian) 2D-gradient record (3 float4 planes) */
 
 enum { I4D_MODE_FULL = 0, I4D_MODE_ISO_ROT = 1, I4D_MODE_ISO_IDENTITY = 2 };
@@ -140,7 +141,7 @@ I4D_API int64_t i4d_param_floats(int32_t sh_deg);
  *   g        host struct, params on the device
  *   views    host; cams: DEVICE array of views->n_views cameras
  *   settings host (NULL = defaults)
- *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 3-plane record layout
+ *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 4-plane record layout
  *   touched  DEVICE out, n_views * n uint32: number of tiles of the record's rectangle
  *            (0 for culled or off-screen Gaussians)
  */

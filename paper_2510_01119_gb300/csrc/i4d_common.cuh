@@ -78,6 +78,17 @@ I4D_D bool eval_fragment(float dx, float dy, float ca, float cb, float cc, float
   return alpha >= s.alpha_min;
 }
 
+// Pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max of a conic, widened by
+// 1% + 0.01 px so that float rounding can never exclude a pixel centre that the per-pixel test
+// accepts (the half-widths are 3 sqrt of the diagonal of the inverse conic).
+I4D_D float4 ellipse_box(float u, float v, float ca, float cb, float cc, float q_max) {
+  const float det = ca * cc - cb * cb;
+  if (!(det > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
+  const float hx = sqrtf(q_max * cc / det) * 1.01f + 0.01f;
+  const float hy = sqrtf(q_max * ca / det) * 1.01f + 0.01f;
+  return make_float4(u - hx, u + hx, v - hy, v + hy);
+}
+
 // device status / error word helpers
 I4D_D void set_status(int32_t* status, int32_t code) {
   if (status) atomicCAS(status, 0, code);

@@ -1,24 +1,21 @@
 // Front-to-back compositing of all views' tiles in one launch, and its backward.
 //
-// One CTA per (view, tile).  Each warp owns an 8x8 pixel block of the tile and each thread two
-// vertically adjacent pixels, so a record fetched from shared memory serves two pixels.  Records of
-// the tile's depth-sorted list are staged in shared memory in batches, together with the bounding
-// box of each Gaussian's 3-sigma ellipse.  Each warp then compacts, in list order, the batch
-// entries whose box meets its 8x8 block (one test per entry spread over the lanes, a ballot and a
-// prefix count), and its pixels visit only those: exact, because the box contains every pixel
-// centre with q <= q_max, and about 40% of a 16x16 tile's list survives for a block.
-// The forward leaves the batch loop once every pixel of the tile is saturated (block vote); the
-// backward walks the list back to front from each pixel's last blended fragment, recovering the
-// transmittance from T_final by division (no per-fragment state), and sums each Gaussian's nine 2D
-// gradient components over the warp with a transposed shuffle reduction (14 shuffles) before nine
-// lanes issue one atomic each.
+// One CTA per (view, tile); each warp owns an 8x8 pixel block of the tile and each thread two
+// vertically adjacent pixels.  The warps of a CTA do not synchronise with one another: each warp
+// streams its tile's depth-sorted list in chunks of 32 entries, one entry per lane, tests the
+// entry's ellipse box (precomputed by slice_project) against its own 8x8 block, and stages only the
+// hits -- compacted in list order by a ballot and a prefix count -- in its private shared-memory
+// slots; its pixels then visit those hits.  The test is exact: the box holds every pixel centre
+// with q <= q_max.  A warp stops as soon as all its pixels are saturated (forward) or when it has
+// passed its pixels' last blended fragments (backward), independently of the other warps.
+// The backward walks the list back to front, recovering the transmittance from T_final by division
+// (no per-fragment state), and sums each Gaussian's nine 2D-gradient components over the warp with
+// a transposed shuffle reduction (14 shuffles) before nine lanes issue one atomic each.
 #include "kernels.cuh"
 
 namespace i4d {
 
 namespace {
-
-constexpr int kBatch = 256;  // records staged per round
 
 struct TileCoord {
   int v, tx, ty, W, H;
@@ -33,33 +30,6 @@ __device__ __forceinline__ TileCoord tile_coord(const ViewTable& vt, int tile) {
   c.W = vt.width[c.v];
   c.H = vt.height[c.v];
   return c;
-}
-
-// Bounding box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max, widened by 1% + 0.01 px so that
-// float rounding can never exclude a pixel centre the per-pixel test would accept.
-__device__ __forceinline__ float4 ellipse_box(float u, float v, float ca, float cb, float cc, float q_max) {
-  const float det = ca * cc - cb * cb;
-  if (!(det > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
-  const float hx = sqrtf(q_max * cc / det) * 1.01f + 0.01f;
-  const float hy = sqrtf(q_max * ca / det) * 1.01f + 0.01f;
-  return make_float4(u - hx, u + hx, v - hy, v + hy);
-}
-
-// Compact, in order, the indices j < m of the batch whose boxes meet the warp's block into list;
-// returns the count (warp-uniform).
-template <class WP>
-__device__ __forceinline__ int warp_candidates(const WP& wp, const float4* sbox, int m, uint8_t* list, int lane) {
-  int cnt = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < m; r += 32) {
-    const int j = r + lane;
-    const bool hit = j < m && !wp.misses(sbox[j]);
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) list[cnt + __popc(mask & lt)] = (uint8_t)j;
-    cnt += __popc(mask);
-  }
-  __syncwarp();
-  return cnt;
 }
 
 // Per-warp geometry: the warp's 8x8 block and the thread's two pixels.
@@ -83,6 +53,15 @@ struct WarpPix {
   }
 };
 
+// A warp's staged hits of one chunk.
+struct WarpStage {
+  float4 a[32];
+  float4 b[32];
+  float c2[32];
+  uint32_t pos[32];
+  uint32_t rec[32];
+};
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
@@ -90,46 +69,44 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
                                                                  float* __restrict__ img, float* __restrict__ T_final,
                                                                  uint32_t* __restrict__ last_out,
                                                                  uint32_t* __restrict__ ncon) {
-  constexpr int NT = TW * TH / 2;
-  __shared__ float4 s0[kBatch];
-  __shared__ float4 s1[kBatch];
-  __shared__ float4 sbox[kBatch];
-  __shared__ float s2[kBatch];
-  __shared__ uint8_t wlist[NT / 32][kBatch];
+  __shared__ WarpStage stage[TW * TH / 64];
   const TileCoord tc = tile_coord(vt, blockIdx.x);
   const WarpPix<TW> wp(tc, TH);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  WarpStage& st = stage[threadIdx.x >> 5];
+  const unsigned lt = (1u << lane) - 1u;
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
   const uint2 rg = ranges[blockIdx.x];
   const size_t VN = (size_t)vt.n_views * n;
-  const size_t base = (size_t)tc.v * n;
+  const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
   const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
   float T0 = 1.0f, T1 = 1.0f;
   float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
   uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
   bool done0 = !in0, done1 = !in1;
-  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(done0 && done1) == NT) break;
-    for (int k = threadIdx.x; k < kBatch; k += NT) {
-      const uint32_t idx = start + k;
-      if (idx < rg.y) {
-        const size_t r = base + __ldg(&ids[idx]);
-        const float4 a = __ldg(&proj[r]);
-        const float4 b = __ldg(&proj[VN + r]);
-        s0[k] = a;
-        s1[k] = b;
-        s2[k] = __ldg(&proj[2 * VN + r]).x;
-        sbox[k] = ellipse_box(a.x, a.y, a.z, a.w, b.x, S.q_max);
-      }
+  for (uint32_t base = rg.x; base < rg.y; base += 32) {
+    if (__all_sync(0xffffffffu, done0 && done1)) break;
+    const uint32_t idx = base + lane;
+    uint32_t r = 0;
+    bool hit = false;
+    if (idx < rg.y) {
+      r = vbase + __ldg(&ids[idx]);
+      hit = !wp.misses(__ldg(&proj[3 * VN + r]));
     }
-    __syncthreads();
-    const int m = min(kBatch, (int)(rg.y - start));
-    const int cand = warp_candidates(wp, sbox, m, wlist[warp], lane);
-    for (int t = 0; t < cand && !(done0 && done1); ++t) {
-      const int j = wlist[warp][t];
-      const float4 a = s0[j];
-      const float4 b = s1[j];
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int k = __popc(mask & lt);
+      st.a[k] = __ldg(&proj[r]);
+      st.b[k] = __ldg(&proj[VN + r]);
+      st.c2[k] = __ldg(&proj[2 * VN + r]).x;
+      st.pos[k] = idx - rg.x;
+    }
+    __syncwarp();
+    const int cnt = __popc(mask);
+    for (int t = 0; t < cnt && !(done0 && done1); ++t) {
+      const float4 a = st.a[t];
+      const float4 b = st.b[t];
       const float dx = __fsub_rn(fx, a.x);
       float q, G, ar, al;
       if (!done0 && eval_fragment(dx, __fsub_rn(fy0, a.y), a.z, a.w, b.x, b.y, S, q, G, ar, al)) {
@@ -140,9 +117,9 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
           const float w = al * T0;
           C00 += w * b.z;
           C01 += w * b.w;
-          C02 += w * s2[j];
+          C02 += w * st.c2[t];
           T0 = Tn;
-          last0 = start + (uint32_t)j - rg.x + 1u;
+          last0 = st.pos[t] + 1u;
           ++cnt0;
         }
       }
@@ -154,13 +131,14 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
           const float w = al * T1;
           C10 += w * b.z;
           C11 += w * b.w;
-          C12 += w * s2[j];
+          C12 += w * st.c2[t];
           T1 = Tn;
-          last1 = start + (uint32_t)j - rg.x + 1u;
+          last1 = st.pos[t] + 1u;
           ++cnt1;
         }
       }
     }
+    __syncwarp();
   }
   const int64_t HW = (int64_t)tc.W * tc.H;
   if (in0) {
@@ -261,22 +239,17 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
                                                                  const uint32_t* __restrict__ last_in,
                                                                  const float* __restrict__ dimg,
                                                                  float* __restrict__ grad2d) {
-  constexpr int NT = TW * TH / 2;
-  __shared__ float4 s0[kBatch];
-  __shared__ float4 s1[kBatch];
-  __shared__ float4 sbox[kBatch];
-  __shared__ float s2[kBatch];
-  __shared__ uint32_t sid[kBatch];
-  __shared__ uint8_t wlist[NT / 32][kBatch];
-  __shared__ uint32_t smax;
+  __shared__ WarpStage stage[TW * TH / 64];
   const TileCoord tc = tile_coord(vt, blockIdx.x);
   const WarpPix<TW> wp(tc, TH);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  WarpStage& st = stage[threadIdx.x >> 5];
+  const unsigned lt = (1u << lane) - 1u;
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
   const uint2 rg = ranges[blockIdx.x];
   const size_t VN = (size_t)vt.n_views * n;
-  const size_t base = (size_t)tc.v * n;
+  const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
   const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
   const int64_t HW = (int64_t)tc.W * tc.H;
   PixBwd P0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, P1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
@@ -304,40 +277,36 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
     P1.S1 = P1.T * S.bg[1];
     P1.S2 = P1.T * S.bg[2];
   }
-  if (threadIdx.x == 0) smax = 0;
-  __syncthreads();
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P0.L, P1.L));
-  if (lane == 0) atomicMax(&smax, wmax);
-  __syncthreads();
-  const uint32_t end = rg.x + min(smax, rg.y - rg.x);  // never past the tile's range
+  // this warp never needs entries past its pixels' last blended fragments
+  const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P0.L, P1.L));
+  const uint32_t end = rg.x + min(wL, rg.y - rg.x);
   // component c of a 2D-gradient record lives in plane c / 4, lane c % 4 (c = 8: plane 2, lane 0)
   const int comp = lane >> 2;
   const size_t comp_off = (size_t)(comp >> 2) * VN * 4 + (comp & 3);
   for (uint32_t hi = end; hi > rg.x;) {
-    const uint32_t lo = (hi - rg.x > (uint32_t)kBatch) ? hi - kBatch : rg.x;
-    __syncthreads();
-    for (int k = threadIdx.x; k < kBatch; k += NT) {
-      const uint32_t idx = lo + k;
-      if (idx < hi) {
-        const uint32_t id = __ldg(&ids[idx]);
-        const size_t r = base + id;
-        const float4 a = __ldg(&proj[r]);
-        const float4 b = __ldg(&proj[VN + r]);
-        s0[k] = a;
-        s1[k] = b;
-        s2[k] = __ldg(&proj[2 * VN + r]).x;
-        sid[k] = id;
-        sbox[k] = ellipse_box(a.x, a.y, a.z, a.w, b.x, S.q_max);
-      }
+    const uint32_t lo = (hi - rg.x > 32u) ? hi - 32u : rg.x;
+    const uint32_t idx = lo + lane;
+    uint32_t r = 0;
+    bool hit = false;
+    if (idx < hi) {
+      r = vbase + __ldg(&ids[idx]);
+      hit = !wp.misses(__ldg(&proj[3 * VN + r]));
     }
-    __syncthreads();
-    const int cand = warp_candidates(wp, sbox, (int)(hi - lo), wlist[warp], lane);
-    for (int t = cand - 1; t >= 0; --t) {  // warp-uniform trip count
-      const int j = wlist[warp][t];
-      const uint32_t pos = lo + (uint32_t)j - rg.x;  // 0-based position in the tile list
-      const float4 a = s0[j];
-      const float4 b = s1[j];
-      const float c2 = s2[j];
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int k = __popc(mask & lt);
+      st.a[k] = __ldg(&proj[r]);
+      st.b[k] = __ldg(&proj[VN + r]);
+      st.c2[k] = __ldg(&proj[2 * VN + r]).x;
+      st.pos[k] = idx - rg.x;
+      st.rec[k] = r;
+    }
+    __syncwarp();
+    for (int t = __popc(mask) - 1; t >= 0; --t) {  // warp-uniform trip count
+      const float4 a = st.a[t];
+      const float4 b = st.b[t];
+      const float c2 = st.c2[t];
+      const uint32_t pos = st.pos[t];
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const float dx = __fsub_rn(fx, a.x);
       bool any = false;
@@ -346,11 +315,12 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
       if (__any_sync(0xffffffffu, any)) {
         const float tot = warp_transpose_sum8(g, lane);
         const float gb = warp_sum(g[8]);
-        const size_t r = base + sid[j];
-        if ((lane & 3) == 0) atomicAdd(&grad2d[comp_off + r * 4], tot);
-        if (lane == 1) atomicAdd(&grad2d[2 * VN * 4 + r * 4], gb);
+        const size_t rr = st.rec[t];
+        if ((lane & 3) == 0) atomicAdd(&grad2d[comp_off + rr * 4], tot);
+        if (lane == 1) atomicAdd(&grad2d[2 * VN * 4 + rr * 4], gb);
       }
     }
+    __syncwarp();
     hi = lo;
   }
 }

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
     proj[r] = make_float4(F.u, F.v, F.conic[0], F.conic[1]);
     proj[VN + r] = make_float4(F.conic[2], F.ot, fmaxf(F.raw[0], 0.0f), fmaxf(F.raw[1], 0.0f));
     proj[2 * VN + r] = make_float4(fmaxf(F.raw[2], 0.0f), F.m[2], F.radius, 0.0f);
+    proj[3 * VN + r] = F.visible ? ellipse_box(F.u, F.v, F.conic[0], F.conic[1], F.conic[2], S.q_max)
+                                 : make_float4(1.0f, 0.0f, 1.0f, 0.0f);
     touched[r] = cnt;
   }
 }

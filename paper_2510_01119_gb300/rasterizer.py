@@ -89,7 +89,7 @@ class Rasterizer:
         self.total_pixels = int(L.load().i4d_total_pixels(ctypes.byref(self.views)))
         VN = self.V * self.n
         dev = self.device
-        self.proj = torch.empty(3 * VN * 4, dtype=torch.float32, device=dev)
+        self.proj = torch.empty(4 * VN * 4, dtype=torch.float32, device=dev)
         self.touched = torch.empty(max(VN, 1), dtype=torch.int32, device=dev)
         self.ranges = torch.empty(2 * max(self.total_tiles, 1), dtype=torch.int32, device=dev)
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)

@@ -65,7 +65,7 @@ def test_slice_project_records_match_oracle(dev, orc, mode, deg):
     cam = synth.camera(128, 96, 60.0, time=0.5)
     rast, _, _ = _gpu_render(g, [cam])
     n = g["mean4"].shape[0]
-    planes = rast.proj.view(3, n, 4).cpu().numpy()
+    planes = rast.proj.view(4, n, 4).cpu().numpy()
     touched = rast.touched[:n].cpu().numpy()
     P = orc.project(g, cam)
     C = orc.P
