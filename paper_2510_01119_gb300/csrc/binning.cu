@@ -245,6 +245,38 @@ __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, const int6
   if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
 }
 
+// Tiles ordered by decreasing list length, in buckets of a quarter octave (order inside a bucket is
+// arbitrary: it only changes which CTA starts first, never a result).  One CTA of 1024 threads.
+constexpr int kOrderBuckets = 80;
+
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+  const int b = (int)floorf(4.0f * log2f((float)len + 1.0f));
+  return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __restrict__ ranges, int T,
+                                                          uint32_t* __restrict__ order) {
+  __shared__ uint32_t hist[kOrderBuckets];
+  for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x)
+    atomicAdd(&hist[length_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < kOrderBuckets; ++k) {
+      const uint32_t c = hist[k];
+      hist[k] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const uint32_t pos = atomicAdd(&hist[length_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+    order[pos] = (uint32_t)t;
+  }
+}
+
 }  // namespace
 
 size_t scan_workspace_bytes(int64_t) { return sizeof(uint64_t) * kScanMaxBlocks; }
@@ -325,6 +357,10 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64
   const int threads = 256;
   const int64_t blocks = (capacity + threads - 1) / threads;
   tile_ranges_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, st>>>(keys, n_dev, capacity, ranges, status);
+  {
+    I4D_PROF("tile_order", st);
+    tile_order_kernel<<<1, 1024, 0, st>>>(ranges, (int)total_tiles, ranges + 2 * total_tiles);
+  }
   return cudaGetLastError();
 }
 

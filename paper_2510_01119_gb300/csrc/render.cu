@@ -1,16 +1,18 @@
 // Front-to-back compositing of all views' tiles in one launch, and its backward.
 //
-// One CTA per (view, tile); each warp owns an 8x8 pixel block of the tile and each thread two
-// vertically adjacent pixels.  The warps of a CTA do not synchronise with one another: each warp
-// streams its tile's depth-sorted list in chunks of 32 entries, one entry per lane, tests the
-// entry's ellipse box (precomputed by slice_project) against its own 8x8 block, and stages only the
-// hits -- compacted in list order by a ballot and a prefix count -- in its private shared-memory
-// slots; its pixels then visit those hits.  The test is exact: the box holds every pixel centre
-// with q <= q_max.  A warp stops as soon as all its pixels are saturated (forward) or when it has
-// passed its pixels' last blended fragments (backward), independently of the other warps.
+// One CTA per (view, tile), taken longest list first.  Each 16-lane half-warp owns an 8x4 pixel
+// block of the tile and each thread two vertically adjacent pixels.  The warps of a CTA never
+// synchronise with one another: each warp streams its tile's depth-sorted list in chunks of 32
+// entries, one entry per lane, tests the entry's ellipse box (precomputed by slice_project) against
+// the blocks of its two halves, and stages the hits of each half -- compacted in list order by a
+// ballot and a prefix count -- in that half's shared-memory slots; each half's pixels then visit
+// only those hits, the two halves side by side.  The test is exact: the box holds every pixel
+// centre with q <= q_max.  A warp stops as soon as all its pixels are saturated (forward) or when
+// it has passed its pixels' last blended fragments (backward).
 // The backward walks the list back to front, recovering the transmittance from T_final by division
-// (no per-fragment state), and sums each Gaussian's nine 2D-gradient components over the warp with
-// a transposed shuffle reduction (14 shuffles) before nine lanes issue one atomic each.
+// (no per-fragment state), and sums each Gaussian's nine 2D-gradient components over its half-warp
+// with a transposed shuffle reduction (12 shuffles serve the two halves' Gaussians at once) before
+// nine lanes of the half issue one atomic each.
 #include "kernels.cuh"
 
 namespace i4d {
@@ -32,29 +34,33 @@ __device__ __forceinline__ TileCoord tile_coord(const ViewTable& vt, int tile) {
   return c;
 }
 
-// Per-warp geometry: the warp's 8x8 block and the thread's two pixels.
+// Geometry of a warp: its two half-warps' 8x4 blocks and the thread's two pixels.
 template <int TW>
 struct WarpPix {
   int px, py0;
-  float wx0, wx1, wy0, wy1;  // pixel-centre extent of the warp's block
+  int half;                       // 0: lanes 0-15, 1: lanes 16-31
+  float hx0, hx1, hy0[2], hy1[2];  // pixel-centre extents of the two halves' blocks
   __device__ __forceinline__ WarpPix(const TileCoord& tc, int TH) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx = tc.tx * TW + (warp % (TW / 8)) * 8;
     const int by = tc.ty * TH + (warp / (TW / 8)) * 8;
+    half = lane >> 4;
     px = bx + (lane & 7);
-    py0 = by + (lane >> 3) * 2;
-    wx0 = (float)bx + 0.5f;
-    wx1 = (float)bx + 7.5f;
-    wy0 = (float)by + 0.5f;
-    wy1 = (float)by + 7.5f;
+    py0 = by + half * 4 + ((lane >> 3) & 1) * 2;
+    hx0 = (float)bx + 0.5f;
+    hx1 = (float)bx + 7.5f;
+    hy0[0] = (float)by + 0.5f;
+    hy1[0] = (float)by + 3.5f;
+    hy0[1] = (float)by + 4.5f;
+    hy1[1] = (float)by + 7.5f;
   }
-  __device__ __forceinline__ bool misses(const float4 b) const {
-    return b.y < wx0 || b.x > wx1 || b.w < wy0 || b.z > wy1;
+  __device__ __forceinline__ bool misses(const float4 b, int h) const {
+    return b.y < hx0 || b.x > hx1 || b.w < hy0[h] || b.z > hy1[h];
   }
 };
 
-// A warp's staged hits of one chunk.
-struct WarpStage {
+// A half-warp's staged hits of one chunk.
+struct HalfStage {
   float4 a[32];
   float4 b[32];
   float c2[32];
@@ -62,22 +68,61 @@ struct WarpStage {
   uint32_t rec[32];
 };
 
+// Stage the chunk [lo, hi) of the tile list: every lane tests one entry against both halves' blocks
+// and writes a hit into the list of each half it meets, in list order.  Returns this half's count.
+template <class WP>
+__device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const float4* __restrict__ proj, size_t VN,
+                                           const uint32_t* __restrict__ ids, uint32_t vbase, uint32_t lo, uint32_t hi,
+                                           uint32_t tile_start, int lane, int& other) {
+  const uint32_t idx = lo + lane;
+  uint32_t r = 0;
+  bool hit0 = false, hit1 = false;
+  if (idx < hi) {
+    r = vbase + __ldg(&ids[idx]);
+    const float4 box = __ldg(&proj[3 * VN + r]);
+    hit0 = !wp.misses(box, 0);
+    hit1 = !wp.misses(box, 1);
+  }
+  const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+  const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+  if (hit0 || hit1) {
+    const unsigned lt = (1u << lane) - 1u;
+    const float4 a = __ldg(&proj[r]);
+    const float4 b = __ldg(&proj[VN + r]);
+    const float c2 = __ldg(&proj[2 * VN + r]).x;
+    const uint32_t pos = idx - tile_start;
+    if (hit0) {
+      const int k = __popc(m0 & lt);
+      st[0].a[k] = a; st[0].b[k] = b; st[0].c2[k] = c2; st[0].pos[k] = pos; st[0].rec[k] = r;
+    }
+    if (hit1) {
+      const int k = __popc(m1 & lt);
+      st[1].a[k] = a; st[1].b[k] = b; st[1].c2[k] = c2; st[1].pos[k] = pos; st[1].rec[k] = r;
+    }
+  }
+  __syncwarp();
+  other = __popc(wp.half ? m0 : m1);
+  return __popc(wp.half ? m1 : m0);
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
-                                                                 const uint2* __restrict__ ranges, Settings S,
+                                                                 const uint32_t* __restrict__ ranges, Settings S,
                                                                  float* __restrict__ img, float* __restrict__ T_final,
                                                                  uint32_t* __restrict__ last_out,
                                                                  uint32_t* __restrict__ ncon) {
-  __shared__ WarpStage stage[TW * TH / 64];
-  const TileCoord tc = tile_coord(vt, blockIdx.x);
+  __shared__ HalfStage stage[TW * TH / 64][2];
+  const int T_all = vt.tile_off[vt.n_views];
+  const int tile = (int)ranges[2 * T_all + blockIdx.x];
+  const TileCoord tc = tile_coord(vt, tile);
   const WarpPix<TW> wp(tc, TH);
   const int lane = threadIdx.x & 31;
-  WarpStage& st = stage[threadIdx.x >> 5];
-  const unsigned lt = (1u << lane) - 1u;
+  HalfStage* st = stage[threadIdx.x >> 5];
+  const HalfStage& mine = st[wp.half];
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
-  const uint2 rg = ranges[blockIdx.x];
+  const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
   const size_t VN = (size_t)vt.n_views * n;
   const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
   const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
@@ -85,28 +130,13 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
   float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
   uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
   bool done0 = !in0, done1 = !in1;
-  for (uint32_t base = rg.x; base < rg.y; base += 32) {
+  for (uint32_t base = rs; base < re; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
-    const uint32_t idx = base + lane;
-    uint32_t r = 0;
-    bool hit = false;
-    if (idx < rg.y) {
-      r = vbase + __ldg(&ids[idx]);
-      hit = !wp.misses(__ldg(&proj[3 * VN + r]));
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const int k = __popc(mask & lt);
-      st.a[k] = __ldg(&proj[r]);
-      st.b[k] = __ldg(&proj[VN + r]);
-      st.c2[k] = __ldg(&proj[2 * VN + r]).x;
-      st.pos[k] = idx - rg.x;
-    }
-    __syncwarp();
-    const int cnt = __popc(mask);
+    int other;
+    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, base, min(base + 32u, re), rs, lane, other);
     for (int t = 0; t < cnt && !(done0 && done1); ++t) {
-      const float4 a = st.a[t];
-      const float4 b = st.b[t];
+      const float4 a = mine.a[t];
+      const float4 b = mine.b[t];
       const float dx = __fsub_rn(fx, a.x);
       float q, G, ar, al;
       if (!done0 && eval_fragment(dx, __fsub_rn(fy0, a.y), a.z, a.w, b.x, b.y, S, q, G, ar, al)) {
@@ -117,9 +147,9 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
           const float w = al * T0;
           C00 += w * b.z;
           C01 += w * b.w;
-          C02 += w * st.c2[t];
+          C02 += w * mine.c2[t];
           T0 = Tn;
-          last0 = st.pos[t] + 1u;
+          last0 = mine.pos[t] + 1u;
           ++cnt0;
         }
       }
@@ -131,9 +161,9 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
           const float w = al * T1;
           C10 += w * b.z;
           C11 += w * b.w;
-          C12 += w * st.c2[t];
+          C12 += w * mine.c2[t];
           T1 = Tn;
-          last1 = st.pos[t] + 1u;
+          last1 = mine.pos[t] + 1u;
           ++cnt1;
         }
       }
@@ -199,55 +229,56 @@ __device__ __forceinline__ bool pixel_grad(PixBwd& P, float dx, float dy, const 
   return true;
 }
 
-// Sum g[0..7] over the warp so that lane l ends up with the total of component l >> 2 (every lane
-// of a group of four holds it): 4 + 2 + 1 + 1 + 1 = 9 shuffles instead of 8 x 5.
-__device__ __forceinline__ float warp_transpose_sum8(const float* g, int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+// Sum g[0..7] over each 16-lane half so that lane l of a half ends up with the half's total of
+// component (l >> 1) & 7 (both lanes of a pair hold it): 4 + 2 + 1 + 1 = 8 shuffles.
+__device__ __forceinline__ float half_transpose_sum8(const float* g, int lane) {
+  const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
   float w[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float send = b4 ? g[k] : g[k + 4];
-    const float keep = b4 ? g[k + 4] : g[k];
-    w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    const float send = b3 ? g[k] : g[k + 4];
+    const float keep = b3 ? g[k + 4] : g[k];
+    w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
   float x[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float send = b3 ? w[k] : w[k + 2];
-    const float keep = b3 ? w[k + 2] : w[k];
-    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    const float send = b2 ? w[k] : w[k + 2];
+    const float keep = b2 ? w[k + 2] : w[k];
+    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
-  const float send = b2 ? x[0] : x[1];
-  const float keep = b2 ? x[1] : x[0];
-  float y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  const float send = b1 ? x[0] : x[1];
+  const float keep = b1 ? x[1] : x[0];
+  float y = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   y += __shfl_xor_sync(0xffffffffu, y, 1);
   return y;
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
+__device__ __forceinline__ float half_sum(float x) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
-                                                                 const uint2* __restrict__ ranges, Settings S,
+                                                                 const uint32_t* __restrict__ ranges, Settings S,
                                                                  const float* __restrict__ T_final,
                                                                  const uint32_t* __restrict__ last_in,
                                                                  const float* __restrict__ dimg,
                                                                  float* __restrict__ grad2d) {
-  __shared__ WarpStage stage[TW * TH / 64];
-  const TileCoord tc = tile_coord(vt, blockIdx.x);
+  __shared__ HalfStage stage[TW * TH / 64][2];
+  const int T_all = vt.tile_off[vt.n_views];
+  const int tile = (int)ranges[2 * T_all + blockIdx.x];
+  const TileCoord tc = tile_coord(vt, tile);
   const WarpPix<TW> wp(tc, TH);
   const int lane = threadIdx.x & 31;
-  WarpStage& st = stage[threadIdx.x >> 5];
-  const unsigned lt = (1u << lane) - 1u;
+  HalfStage* st = stage[threadIdx.x >> 5];
+  const HalfStage& mine = st[wp.half];
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
-  const uint2 rg = ranges[blockIdx.x];
+  const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
   const size_t VN = (size_t)vt.n_views * n;
   const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
   const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
@@ -279,45 +310,39 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   }
   // this warp never needs entries past its pixels' last blended fragments
   const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P0.L, P1.L));
-  const uint32_t end = rg.x + min(wL, rg.y - rg.x);
+  const uint32_t end = rs + min(wL, re - rs);
   // component c of a 2D-gradient record lives in plane c / 4, lane c % 4 (c = 8: plane 2, lane 0)
-  const int comp = lane >> 2;
+  const int comp = (lane >> 1) & 7;
   const size_t comp_off = (size_t)(comp >> 2) * VN * 4 + (comp & 3);
-  for (uint32_t hi = end; hi > rg.x;) {
-    const uint32_t lo = (hi - rg.x > 32u) ? hi - 32u : rg.x;
-    const uint32_t idx = lo + lane;
-    uint32_t r = 0;
-    bool hit = false;
-    if (idx < hi) {
-      r = vbase + __ldg(&ids[idx]);
-      hit = !wp.misses(__ldg(&proj[3 * VN + r]));
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const int k = __popc(mask & lt);
-      st.a[k] = __ldg(&proj[r]);
-      st.b[k] = __ldg(&proj[VN + r]);
-      st.c2[k] = __ldg(&proj[2 * VN + r]).x;
-      st.pos[k] = idx - rg.x;
-      st.rec[k] = r;
-    }
-    __syncwarp();
-    for (int t = __popc(mask) - 1; t >= 0; --t) {  // warp-uniform trip count
-      const float4 a = st.a[t];
-      const float4 b = st.b[t];
-      const float c2 = st.c2[t];
-      const uint32_t pos = st.pos[t];
+  const bool comp_lane = (lane & 1) == 0;
+  const bool gb_lane = (lane & 15) == 1;
+  for (uint32_t hi = end; hi > rs;) {
+    const uint32_t lo = (hi - rs > 32u) ? hi - 32u : rs;
+    int other;
+    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, lo, hi, rs, lane, other);
+    const int trips = max(cnt, other);  // warp-uniform
+    for (int t = trips - 1; t >= 0; --t) {
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const float dx = __fsub_rn(fx, a.x);
       bool any = false;
-      if (in0 && pos < P0.L) any |= pixel_grad(P0, dx, __fsub_rn(fy0, a.y), a, b, c2, S, g);
-      if (in1 && pos < P1.L) any |= pixel_grad(P1, dx, __fsub_rn(fy1, a.y), a, b, c2, S, g);
-      if (__any_sync(0xffffffffu, any)) {
-        const float tot = warp_transpose_sum8(g, lane);
-        const float gb = warp_sum(g[8]);
-        const size_t rr = st.rec[t];
-        if ((lane & 3) == 0) atomicAdd(&grad2d[comp_off + rr * 4], tot);
-        if (lane == 1) atomicAdd(&grad2d[2 * VN * 4 + rr * 4], gb);
+      uint32_t rr = 0;
+      if (t < cnt) {
+        const float4 a = mine.a[t];
+        const float4 b = mine.b[t];
+        const float c2 = mine.c2[t];
+        const uint32_t pos = mine.pos[t];
+        rr = mine.rec[t];
+        const float dx = __fsub_rn(fx, a.x);
+        if (in0 && pos < P0.L) any |= pixel_grad(P0, dx, __fsub_rn(fy0, a.y), a, b, c2, S, g);
+        if (in1 && pos < P1.L) any |= pixel_grad(P1, dx, __fsub_rn(fy1, a.y), a, b, c2, S, g);
+      }
+      const unsigned vm = __ballot_sync(0xffffffffu, any);
+      if (vm) {
+        const float tot = half_transpose_sum8(g, lane);
+        const float gb = half_sum(g[8]);
+        if ((vm >> (16 * wp.half)) & 0xffffu) {  // this half has a contribution
+          if (comp_lane) atomicAdd(&grad2d[comp_off + (size_t)rr * 4], tot);
+          if (gb_lane) atomicAdd(&grad2d[2 * VN * 4 + (size_t)rr * 4], gb);
+        }
       }
     }
     __syncwarp();
@@ -332,8 +357,7 @@ cudaError_t launch_fwd_t(const ViewTable& vt, int n, const float* proj, const ui
   const int tiles = vt.tile_off[vt.n_views];
   I4D_PROF("render_fwd", st);
   render_fwd_kernel<TW, TH><<<tiles, TW * TH / 2, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
-                                                            reinterpret_cast<const uint2*>(ranges), S, img, T_final,
-                                                            last, n_contrib);
+                                                            ranges, S, img, T_final, last, n_contrib);
   return cudaGetLastError();
 }
 
@@ -344,8 +368,7 @@ cudaError_t launch_bwd_t(const ViewTable& vt, int n, const float* proj, const ui
   const int tiles = vt.tile_off[vt.n_views];
   I4D_PROF("render_bwd", st);
   render_bwd_kernel<TW, TH><<<tiles, TW * TH / 2, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
-                                                            reinterpret_cast<const uint2*>(ranges), S, T_final, last,
-                                                            dL_dimg, grad2d);
+                                                            ranges, S, T_final, last, dL_dimg, grad2d);
   return cudaGetLastError();
 }
 

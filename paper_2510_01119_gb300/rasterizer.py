@@ -91,7 +91,7 @@ class Rasterizer:
         dev = self.device
         self.proj = torch.empty(4 * VN * 4, dtype=torch.float32, device=dev)
         self.touched = torch.empty(max(VN, 1), dtype=torch.int32, device=dev)
-        self.ranges = torch.empty(2 * max(self.total_tiles, 1), dtype=torch.int32, device=dev)
+        self.ranges = torch.empty(3 * max(self.total_tiles, 1), dtype=torch.int32, device=dev)
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.img = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=dev)
@@ -165,7 +165,7 @@ class Rasterizer:
         """Host copy of the sorted (tile, id) pairs: (tiles int64, ids int64)."""
         n = min(int(self.n_inst.item()), self.capacity)
         ids = self.ids[:n].cpu().numpy().astype(np.int64)
-        rg = self.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+        rg = self.ranges[:2 * self.total_tiles].view(-1, 2).cpu().numpy().astype(np.int64)
         tiles = np.zeros(n, np.int64)
         for t in np.nonzero(rg[:, 1] > rg[:, 0])[0]:
             tiles[rg[t, 0]:rg[t, 1]] = t
