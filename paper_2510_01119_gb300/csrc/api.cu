@@ -134,14 +134,7 @@ int32_t i4d_slice_project(const i4d_gaussians* g, const i4d_views* views, const 
 size_t i4d_bin_tiles_workspace_size(const i4d_views* views, int32_t n, int64_t capacity) {
   ViewTable vt;
   if (!make_view_table(views, vt) || n < 0 || capacity < 0) return 0;
-  const int64_t VN = (int64_t)vt.n_views * n;
-  size_t b = 0;
-  b += align256(4 * (size_t)(VN > 0 ? VN : 1));           // offsets
-  b += align256(scan_workspace_bytes(VN));                  // scan partials
-  b += 2 * align256(8 * (size_t)(capacity > 0 ? capacity : 1));  // keys, keys_alt
-  b += 2 * align256(4 * (size_t)(capacity > 0 ? capacity : 1));  // vals, vals_alt
-  b += align256(radix_workspace_bytes(capacity));
-  return b;
+  return bin_workspace_bytes((int64_t)vt.n_views * n, capacity);
 }
 
 int32_t i4d_bin_tiles(const i4d_views* views, int32_t n, const float* proj, const uint32_t* touched,
@@ -149,35 +142,11 @@ int32_t i4d_bin_tiles(const i4d_views* views, int32_t n, const float* proj, cons
                       size_t ws_bytes, void* stream) {
   ViewTable vt;
   if (!make_view_table(views, vt) || n < 0 || capacity < 1 || capacity >= (1ll << 32)) return I4D_ERR_ARG;
+  if ((int64_t)vt.n_views * n >= (1ll << 32)) return I4D_ERR_ARG;
   if (!proj || !touched || !ids || !ranges || !n_inst || !status || !ws) return I4D_ERR_ARG;
   if (ws_bytes < i4d_bin_tiles_workspace_size(views, n, capacity)) return I4D_ERR_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int64_t VN = (int64_t)vt.n_views * n;
-  char* p = reinterpret_cast<char*>(ws);
-  uint32_t* offs = reinterpret_cast<uint32_t*>(p);
-  p += align256(4 * (size_t)(VN > 0 ? VN : 1));
-  void* scan_ws = p;
-  p += align256(scan_workspace_bytes(VN));
-  uint64_t* keys = reinterpret_cast<uint64_t*>(p);
-  p += align256(8 * (size_t)capacity);
-  uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
-  p += align256(8 * (size_t)capacity);
-  uint32_t* vals = reinterpret_cast<uint32_t*>(p);
-  p += align256(4 * (size_t)capacity);
-  uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
-  p += align256(4 * (size_t)capacity);
-  void* radix_ws = p;
-
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
-  if (e == cudaSuccess) e = launch_scan_u32(touched, offs, VN, n_inst, scan_ws, st);
-  if (e == cudaSuccess) e = launch_emit_keys(vt, n, proj, touched, offs, capacity, keys, vals, st);
-  uint64_t* sorted_keys = nullptr;
-  const int bits = 32 + bits_for(vt.tile_off[vt.n_views]);
-  if (e == cudaSuccess)
-    e = launch_radix_sort(keys, vals, keys_alt, vals_alt, ids, capacity, n_inst, bits, radix_ws, &sorted_keys, st);
-  if (e == cudaSuccess)
-    e = launch_tile_ranges(sorted_keys, n_inst, capacity, ranges, vt.tile_off[vt.n_views], status, st);
-  return cuda_status(e);
+  return cuda_status(
+      launch_bin_tiles(vt, n, proj, touched, capacity, ids, ranges, n_inst, status, ws, (cudaStream_t)stream));
 }
 
 int32_t i4d_render_fwd(const i4d_views* views, int32_t n, const float* proj, const uint32_t* ids,

@@ -45,11 +45,30 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t x, uint64_t& excl) 
   return total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
-                                                                   int64_t chunk, uint64_t* __restrict__ bsum) {
+// Element loaders of the scan: the value itself, 1 for a nonzero value, or a value gathered
+// through an index array.
+struct LoadPlain {
+  const uint32_t* p;
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i]; }
+};
+struct LoadNonzero {
+  const uint32_t* p;
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i] != 0u ? 1u : 0u; }
+};
+struct LoadGather {
+  const uint32_t* idx;
+  const uint32_t* p;
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[idx[i]]; }
+};
+
+template <class Load>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load in, const int64_t* __restrict__ n_dev,
+                                                                   int64_t n_max, int64_t chunk,
+                                                                   uint64_t* __restrict__ bsum) {
+  const int64_t n = n_dev ? min(*n_dev, n_max) : n_max;
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(lo + chunk, n);
   uint64_t s = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += in[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += in(i);
   __shared__ uint64_t red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -73,9 +92,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint64_t* __rest
   if (threadIdx.x == 0 && total) *total = (int64_t)tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ in,
-                                                                 uint32_t* __restrict__ out, int64_t n, int64_t chunk,
-                                                                 const uint64_t* __restrict__ bsum) {
+template <class Load>
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(Load in, uint32_t* __restrict__ out,
+                                                                 const int64_t* __restrict__ n_dev, int64_t n_max,
+                                                                 int64_t chunk, const uint64_t* __restrict__ bsum) {
+  const int64_t n = n_dev ? min(*n_dev, n_max) : n_max;
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(lo + chunk, n);
   uint64_t carry = bsum[blockIdx.x];
   for (int64_t base = lo; base < hi; base += kScanTile) {
@@ -84,7 +105,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
     const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      v[k] = (i0 + k < hi) ? in[i0 + k] : 0u;
+      v[k] = (i0 + k < hi) ? in(i0 + k) : 0u;
       s += v[k];
     }
     uint64_t ex;
@@ -109,29 +130,42 @@ void scan_geometry(int64_t n, int& nb, int64_t& chunk) {
   if (nb < 1) nb = 1;
 }
 
-// ---- key emission ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) emit_keys_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
-                                                        const uint32_t* __restrict__ touched,
-                                                        const uint32_t* __restrict__ offsets, int64_t capacity,
-                                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t VN = (int64_t)vt.n_views * n;
+// ---- visible records, emission in depth order ----------------------------------------------------
+// keys[k] = float bits of the depth of the k-th visible record (records in index order), vals[k] = r
+__global__ void __launch_bounds__(256) visible_compact_kernel(int64_t VN, const float4* __restrict__ proj,
+                                                              const uint32_t* __restrict__ touched,
+                                                              const uint32_t* __restrict__ offs,
+                                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= VN) return;
-  const uint32_t cnt = touched[r];
-  if (cnt == 0) return;
-  const int v = (int)(r / n);
-  const uint32_t id = (uint32_t)(r - (int64_t)v * n);
+  if (r >= VN || touched[r] == 0) return;
+  const uint32_t k = offs[r];
+  keys[k] = __float_as_uint(proj[2 * VN + r].y);  // positive depths: float bits order as the values
+  vals[k] = (uint32_t)r;
+}
+
+// Every (tile, Gaussian) pair of the k-th depth-ordered record's rectangle, at offs[k]: key = global
+// tile index, value = Gaussian id.
+__global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
+                                                          const int64_t* __restrict__ R_dev,
+                                                          const uint32_t* __restrict__ rec,
+                                                          const uint32_t* __restrict__ offs, int64_t capacity,
+                                                          uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t VN = (int64_t)vt.n_views * n;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= *R_dev) return;
+  const uint32_t r = rec[k];
+  const int v = (int)(r / (uint32_t)n);
+  const uint32_t id = r - (uint32_t)v * (uint32_t)n;
   const float4 a = proj[r];
   const float4 c = proj[2 * VN + r];
   int x0, y0, x1, y1;
   tile_rect(a.x, a.y, c.z, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
-  const uint64_t dbits = (uint64_t)__float_as_uint(c.y);
-  int64_t o = offsets[r];
-  const int base = vt.tile_off[v];
+  int64_t o = offs[k];
+  const uint32_t base = (uint32_t)vt.tile_off[v];
   for (int ty = y0; ty < y1; ++ty)
     for (int tx = x0; tx < x1; ++tx) {
       if (o < capacity) {
-        keys[o] = ((uint64_t)(base + ty * vt.tiles_x[v] + tx) << 32) | dbits;
+        keys[o] = base + (uint32_t)(ty * vt.tiles_x[v] + tx);
         vals[o] = id;
       }
       ++o;
@@ -150,7 +184,8 @@ __device__ __forceinline__ int64_t live_count(const int64_t* n_dev, int64_t capa
   return n < capacity ? n : capacity;
 }
 
-__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
+template <class K>
+__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restrict__ keys,
                                                                 const int64_t* __restrict__ n_dev, int64_t capacity,
                                                                 int shift, int nblocks, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kRsWarps][kRsBins];
@@ -178,8 +213,9 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const uint64_t* 
 // Stable scatter: warp w ranks the keys of its contiguous 512-key segment in order, using warp-private
 // digit counters; a per-digit exclusive scan over the warps then places each warp's keys after those of
 // the earlier warps, and the scanned histogram places the block after the earlier blocks.
+template <class K>
 __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, const int64_t* __restrict__ n_dev, int64_t capacity, int shift, int nblocks,
     const uint32_t* __restrict__ offs) {
   __shared__ uint32_t cnt[kRsWarps][kRsBins];
@@ -191,14 +227,14 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t seg = lo + (int64_t)warp * (32 * kRsItems);
-  uint64_t key[kRsItems];
+  K key[kRsItems];
   uint32_t val[kRsItems];
   uint32_t rank[kRsItems];
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
     const int64_t i = seg + j * 32 + lane;
     const bool ok = i < n;
-    key[j] = ok ? kin[i] : 0ull;
+    key[j] = ok ? kin[i] : (K)0;
     val[j] = ok ? vin[i] : 0u;
     const uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & 0xffu) : 0x100u;  // 256 = padding
     const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -233,16 +269,16 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
 }
 
 // ---- tile ranges ------------------------------------------------------------------------------------------
-__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ n_dev,
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* __restrict__ n_dev,
                                    int64_t capacity, uint32_t* __restrict__ ranges, int32_t* __restrict__ status) {
   const int64_t total = *n_dev;
   const int64_t n = total < capacity ? total : capacity;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && total > capacity) set_status(status, I4D_ERR_CAPACITY);
   if (i >= n) return;
-  const uint32_t t = (uint32_t)(keys[i] >> 32);
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (int64_t)t] = (uint32_t)i;
-  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+  const uint32_t t = keys[i];
+  if (i == 0 || keys[i - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
 }
 
 // Tiles ordered by decreasing list length, in buckets of a quarter octave (order inside a bucket is
@@ -281,20 +317,28 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __rest
 
 size_t scan_workspace_bytes(int64_t) { return sizeof(uint64_t) * kScanMaxBlocks; }
 
-cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st) {
+namespace {
+template <class Load>
+cudaError_t scan_impl(Load in, uint32_t* out, int64_t n_max, const int64_t* n_dev, int64_t* total, void* ws,
+                      cudaStream_t st) {
   uint64_t* bsum = reinterpret_cast<uint64_t*>(ws);
   int nb;
   int64_t chunk;
-  scan_geometry(n, nb, chunk);
-  if (n == 0) {
+  scan_geometry(n_max, nb, chunk);
+  if (n_max == 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
     return cudaSuccess;
   }
   I4D_PROF("scan", st);
-  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, chunk, bsum);
+  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n_dev, n_max, chunk, bsum);
   scan_top_kernel<<<1, kScanThreads, 0, st>>>(bsum, nb, total);
-  scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n, chunk, bsum);
+  scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n_dev, n_max, chunk, bsum);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st) {
+  return scan_impl(LoadPlain{in}, out, n, nullptr, total, ws, st);
 }
 
 size_t radix_workspace_bytes(int64_t capacity) {
@@ -306,50 +350,112 @@ size_t radix_workspace_bytes(int64_t capacity) {
   return b;
 }
 
-cudaError_t launch_radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                              uint32_t* vals_out, int64_t capacity, const int64_t* n_dev, int bits, void* ws,
-                              uint64_t** keys_result, cudaStream_t st) {
+// vals_out must be a buffer of its own (neither vals nor vals_alt): the last pass reads one of those.
+template <class K>
+cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint32_t* vals_out,
+                              int64_t capacity, const int64_t* n_dev, int bits, void* ws, K** keys_result,
+                              cudaStream_t st) {
   const int64_t nb64 = (capacity + kRsTile - 1) / kRsTile;
   const int nblocks = (int)(nb64 > 0 ? nb64 : 1);
   const int64_t hist_n = (int64_t)kRsBins * nblocks;
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
   size_t off = (sizeof(uint32_t) * (size_t)hist_n + 255) & ~(size_t)255;
   void* scan_ws = reinterpret_cast<char*>(ws) + off;
-  const int passes = (bits + 7) / 8;
-  uint64_t* kb[2] = {keys, keys_alt};
+  const int passes = bits > 0 ? (bits + 7) / 8 : 1;
+  K* kb[2] = {keys, keys_alt};
   uint32_t* vb[2] = {vals, vals_alt};
   for (int p = 0; p < passes; ++p) {
-    const uint64_t* kin = kb[p & 1];
+    const K* kin = kb[p & 1];
     const uint32_t* vin = (p == 0) ? vals : vb[p & 1];
-    uint64_t* kout = kb[(p + 1) & 1];
+    K* kout = kb[(p + 1) & 1];
     uint32_t* vout = (p == passes - 1) ? vals_out : vb[(p + 1) & 1];
     {
       I4D_PROF("radix_hist", st);
-      radix_hist_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, n_dev, capacity, 8 * p, nblocks, hist);
+      radix_hist_kernel<K><<<nblocks, kRsThreads, 0, st>>>(kin, n_dev, capacity, 8 * p, nblocks, hist);
     }
     cudaError_t e = launch_scan_u32(hist, hist, hist_n, nullptr, scan_ws, st);
     if (e != cudaSuccess) return e;
     I4D_PROF("radix_scatter", st);
-    radix_scatter_kernel<<<nblocks, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, capacity, 8 * p, nblocks, hist);
+    radix_scatter_kernel<K><<<nblocks, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, capacity, 8 * p, nblocks,
+                                                            hist);
   }
   if (keys_result) *keys_result = kb[passes & 1];
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_keys(const ViewTable& vt, int n, const float* proj, const uint32_t* touched,
-                             const uint32_t* offsets, int64_t capacity, uint64_t* keys, uint32_t* vals,
-                             cudaStream_t st) {
-  const int64_t VN = (int64_t)vt.n_views * n;
-  if (VN == 0) return cudaSuccess;
-  I4D_PROF("emit_keys", st);
-  const int threads = 256;
-  const int64_t blocks = (VN + threads - 1) / threads;
-  emit_keys_kernel<<<(unsigned)blocks, threads, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), touched,
-                                                         offsets, capacity, keys, vals);
-  return cudaGetLastError();
+template cudaError_t launch_radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
+                                                 const int64_t*, int, void*, uint32_t**, cudaStream_t);
+template cudaError_t launch_radix_sort<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, uint32_t*, int64_t,
+                                                 const int64_t*, int, void*, uint64_t**, cudaStream_t);
+
+size_t bin_workspace_bytes(int64_t VN, int64_t capacity) {
+  const size_t vn = (size_t)(VN > 0 ? VN : 1), cap = (size_t)(capacity > 0 ? capacity : 1);
+  auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t b = 0;
+  b += 7 * a(4 * vn);                   // flag offsets, depth keys x2, record values x3, emit offsets
+  b += a(8);                            // visible-record count
+  b += a(scan_workspace_bytes(VN));
+  b += 4 * a(4 * cap);                  // tile keys x2, id values x2 (the sorted ids go to the output)
+  b += a(radix_workspace_bytes(VN > capacity ? VN : capacity));
+  return b;
 }
 
-cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
+cudaError_t launch_bin_tiles(const ViewTable& vt, int n, const float* proj_f, const uint32_t* touched,
+                             int64_t capacity, uint32_t* ids, uint32_t* ranges, int64_t* n_inst, int32_t* status,
+                             void* ws, cudaStream_t st) {
+  const int64_t VN = (int64_t)vt.n_views * n;
+  const int64_t T = vt.tile_off[vt.n_views];
+  const float4* proj = reinterpret_cast<const float4*>(proj_f);
+  auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* p = reinterpret_cast<char*>(ws);
+  const size_t vn = (size_t)(VN > 0 ? VN : 1), cap = (size_t)(capacity > 0 ? capacity : 1);
+  uint32_t* offs1 = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* dkA = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* dkB = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* dvA = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* dvB = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* dvOut = (uint32_t*)p; p += a(4 * vn);
+  uint32_t* offs2 = (uint32_t*)p; p += a(4 * vn);
+  int64_t* R_dev = (int64_t*)p; p += a(8);
+  void* scan_ws = p; p += a(scan_workspace_bytes(VN));
+  uint32_t* tkA = (uint32_t*)p; p += a(4 * cap);
+  uint32_t* tkB = (uint32_t*)p; p += a(4 * cap);
+  uint32_t* tvA = (uint32_t*)p; p += a(4 * cap);
+  uint32_t* tvB = (uint32_t*)p; p += a(4 * cap);
+  void* radix_ws = p;
+
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  // 1. visible records (touched > 0) in index order, keyed by depth
+  e = scan_impl(LoadNonzero{touched}, offs1, VN, nullptr, R_dev, scan_ws, st);
+  if (e != cudaSuccess) return e;
+  if (VN > 0) {
+    I4D_PROF("visible_compact", st);
+    visible_compact_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(VN, proj, touched, offs1, dkA, dvA);
+  }
+  // 2. stable sort of the visible records by depth (equal depths keep index order)
+  e = launch_radix_sort<uint32_t>(dkA, dvA, dkB, dvB, dvOut, VN, R_dev, 32, radix_ws, nullptr, st);
+  if (e != cudaSuccess) return e;
+  uint32_t* rec_sorted = dvOut;
+  // 3. tile counts in depth order -> output offsets; the total is the instance count
+  e = scan_impl(LoadGather{rec_sorted, touched}, offs2, VN, R_dev, n_inst, scan_ws, st);
+  if (e != cudaSuccess) return e;
+  if (VN > 0) {
+    I4D_PROF("emit_keys", st);
+    emit_sorted_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(vt, n, proj, R_dev, rec_sorted, offs2, capacity,
+                                                                     tkA, tvA);
+  }
+  // 4. stable sort of the pairs by tile: within a tile they stay in (depth, id) order
+  int bits = 0;
+  while ((1ll << bits) < T) ++bits;
+  uint32_t* sorted_tiles = nullptr;
+  e = launch_radix_sort<uint32_t>(tkA, tvA, tkB, tvB, ids, capacity, n_inst, bits, radix_ws, &sorted_tiles, st);
+  if (e != cudaSuccess) return e;
+  // 5. per-tile ranges and the longest-first tile order
+  return launch_tile_ranges(sorted_tiles, n_inst, capacity, ranges, T, status, st);
+}
+
+cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
                                int64_t total_tiles, int32_t* status, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, st);
   if (e != cudaSuccess) return e;

@@ -17,16 +17,20 @@ cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int
 size_t scan_workspace_bytes(int64_t n);
 cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st);
 
-// stable LSD radix sort of (key, value) pairs on bits [0, bits); the count is min(*n_dev, capacity)
+// stable LSD radix sort of (key, value) pairs on bits [0, bits), 8 bits per pass; the count is
+// min(*n_dev, capacity); the values of the last pass go to vals_out
 size_t radix_workspace_bytes(int64_t capacity);
-cudaError_t launch_radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                              uint32_t* vals_out, int64_t capacity, const int64_t* n_dev, int bits, void* ws,
-                              uint64_t** keys_result, cudaStream_t st);
+template <class K>
+cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint32_t* vals_out,
+                              int64_t capacity, const int64_t* n_dev, int bits, void* ws, K** keys_result,
+                              cudaStream_t st);
 
-cudaError_t launch_emit_keys(const ViewTable& vt, int n, const float* proj, const uint32_t* touched,
-                             const uint32_t* offsets, int64_t capacity, uint64_t* keys, uint32_t* vals,
-                             cudaStream_t st);
-cudaError_t launch_tile_ranges(const uint64_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
+// tile binning (visible records sorted by depth, pairs emitted in that order, stable sort by tile)
+size_t bin_workspace_bytes(int64_t VN, int64_t capacity);
+cudaError_t launch_bin_tiles(const ViewTable& vt, int n, const float* proj, const uint32_t* touched,
+                             int64_t capacity, uint32_t* ids, uint32_t* ranges, int64_t* n_inst, int32_t* status,
+                             void* ws, cudaStream_t st);
+cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_dev, int64_t capacity, uint32_t* ranges,
                                int64_t total_tiles, int32_t* status, cudaStream_t st);
 
 cudaError_t launch_render_fwd(const ViewTable& vt, int n, const float* proj, const uint32_t* ids,

@@ -326,8 +326,8 @@ cudaError_t launch_prune(const float* depth, const uint8_t* rgb8, const uint8_t*
     I4D_PROF("prune_compact", st);
     table_compact_kernel<<<(unsigned)sblocks, threads, 0, st>>>(w.T, w.flags, w.offs, cap_int, w.sk[0], w.sv[0]);
   }
-  e = launch_radix_sort(w.sk[0], w.sv[0], w.sk[1], w.sv[1], w.sorted_slots, cap_int, w.total, 32, w.radix_ws,
-                        nullptr, st);
+  e = launch_radix_sort<uint64_t>(w.sk[0], w.sv[0], w.sk[1], w.sv[1], w.sorted_slots, cap_int, w.total, 32,
+                                  w.radix_ws, nullptr, st);
   if (e != cudaSuccess) return e;
   const int64_t oblocks = (capacity + threads - 1) / threads;
   I4D_PROF("prune_gather", st);
