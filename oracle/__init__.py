@@ -122,9 +122,12 @@ def project(g: dict, cam: dict, tile=(16, 16), settings=None) -> np.ndarray:
     return out
 
 
-def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=None, depth_margin=False):
+def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=None, depth_margin=False,
+           impact_min: float = 0.0):
     """Per-pixel depth-sorted compositing -> (img (npix,3), T_final, n_contrib, margin), plus the
-    depth-order margin (smallest relative depth gap between two fragments) when depth_margin."""
+    depth-order margin when depth_margin.  margin / depth margin: smallest relative distance from a
+    threshold / smallest relative depth gap of two consecutive blended fragments, over the decisions
+    whose flip could move the pixel's colour by more than impact_min."""
     lib = _load()
     n = proj.shape[0]
     W, H = int(cam["W"]), int(cam["H"])
@@ -137,7 +140,8 @@ def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=N
     mg = np.zeros(npix, dtype=np.float64)
     dmg = np.zeros(npix, dtype=np.float64)
     rc = lib.orc_render(n, _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S),
-                        npix, _ptr(pix_arr), _ptr(img), _ptr(T), _ptr(nc), _ptr(mg), _ptr(dmg))
+                        npix, _ptr(pix_arr), ctypes.c_double(impact_min), _ptr(img), _ptr(T), _ptr(nc), _ptr(mg),
+                        _ptr(dmg))
     if rc != 0:
         raise RuntimeError(f"orc_render failed ({rc})")
     return (img, T, nc, mg, dmg) if depth_margin else (img, T, nc, mg)

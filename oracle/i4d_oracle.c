@@ -374,7 +374,7 @@ int orc_project(int n, int sh_deg, int mode, const double* mean4, const double* 
 /* ------------------------------------------------------------------------------------------ */
 /* Per-pixel compositing                                                                        */
 /* ------------------------------------------------------------------------------------------ */
-typedef struct { double depth; int id; double q, alpha, g; } frag;
+typedef struct { double depth; int id; double q, alpha, g, margin; int kept; } frag;
 
 static int frag_cmp(const void* pa, const void* pb) {
   const frag* a = (const frag*)pa;
@@ -384,45 +384,97 @@ static int frag_cmp(const void* pa, const void* pb) {
   return (a->id > b->id) - (a->id < b->id);
 }
 
+/* fragments closer than this (relative) to a threshold are reported as candidates for a flip */
+#define NEAR_MARGIN 1e-3
+
 /*
- * Collect the fragments of pixel (px, py): every visible Gaussian whose 3-sigma ellipse covers
- * the pixel centre (q <= q_max) and whose alpha = min(alpha_max, o_t exp(-q/2)) reaches
- * alpha_min, sorted by (depth, id).  *margin collects the smallest relative distance of any
- * of these decisions from its threshold, *dmargin the smallest relative gap between the depths of
- * two fragments (both used to explain FP32-vs-FP64 differences).
+ * Collect the fragments of pixel (px, py), sorted by (depth, id): every visible Gaussian whose
+ * 3-sigma ellipse covers the pixel centre (q <= q_max) and whose alpha = min(alpha_max,
+ * o_t exp(-q/2)) reaches alpha_min (kept = 1), plus the Gaussians that miss one of these tests, or
+ * the o_t cull or the near plane, by less than NEAR_MARGIN relative (kept = 0).  Each fragment
+ * carries the smallest relative distance of its own decisions from their thresholds.
  */
-static int gather_pixel(int n, const double* P, const double* S, int px, int py, frag* buf, double* margin,
-                        double* dmargin) {
+static int gather_pixel(int n, const double* P, const double* S, int px, int py, frag* buf) {
   const double cxp = px + 0.5, cyp = py + 0.5;
   int cnt = 0;
   for (int i = 0; i < n; ++i) {
     const double* r = P + (size_t)i * P_STRIDE;
     const int vis = r[P_VISIBLE] != 0.0;
-    if (!vis && !(r[P_MARGIN] < 1e-3)) continue;
+    if (!vis && !(r[P_MARGIN] < NEAR_MARGIN)) continue;
     if (r[P_DEPTH] <= 0.0 || !(r[P_CA] > 0.0)) continue;
     const double dx = cxp - r[P_U], dy = cyp - r[P_V];
     const double q = r[P_CA] * dx * dx + 2.0 * r[P_CB] * dx * dy + r[P_CC] * dy * dy;
-    if (q > S[S_Q_MAX] * 1.001) continue;
+    if (q > S[S_Q_MAX] * (1.0 + NEAR_MARGIN)) continue;
     const double g = exp(-0.5 * q);
     const double a_raw = r[P_OT] * g;
-    *margin = fmin(*margin, rel_margin(q, S[S_Q_MAX]));
-    if (!vis) { *margin = fmin(*margin, r[P_MARGIN]); continue; }
-    if (q > S[S_Q_MAX]) continue;
-    *margin = fmin(*margin, rel_margin(a_raw, S[S_ALPHA_MIN]));
-    *margin = fmin(*margin, r[P_MARGIN]);
     const double alpha = a_raw < S[S_ALPHA_MAX] ? a_raw : S[S_ALPHA_MAX];
-    if (alpha < S[S_ALPHA_MIN]) continue;
+    double m = fmin(rel_margin(q, S[S_Q_MAX]), r[P_MARGIN]);
+    m = fmin(m, rel_margin(a_raw, S[S_ALPHA_MIN]));
+    const int kept = vis && q <= S[S_Q_MAX] && alpha >= S[S_ALPHA_MIN];
+    if (!kept && !(m < NEAR_MARGIN)) continue;
     buf[cnt].depth = r[P_DEPTH];
     buf[cnt].id = i;
     buf[cnt].q = q;
     buf[cnt].alpha = alpha;
     buf[cnt].g = g;
+    buf[cnt].margin = m;
+    buf[cnt].kept = kept;
     ++cnt;
   }
   qsort(buf, cnt, sizeof(frag), frag_cmp);
-  for (int k = 0; k + 1 < cnt; ++k)
-    *dmargin = fmin(*dmargin, fabs(buf[k + 1].depth - buf[k].depth) / buf[k].depth);
   return cnt;
+}
+
+static double colour_scale(const double* r) {
+  double c = 1.0;
+  for (int ch = P_R; ch <= P_B; ++ch) c = fmax(c, fabs(r[ch]));
+  return c;
+}
+
+/*
+ * Walk the sorted fragments as the compositing does and report, for the decisions whose flip could
+ * change the pixel by more than impact_min, the smallest relative distance from a threshold (*mg:
+ * q, alpha, cull, near plane, the T stop) and the smallest relative depth gap between two
+ * consecutive blended fragments (*dmg).  A fragment of weight T alpha moves the colour by at most
+ * T alpha max(1, |c|) when it enters or leaves; swapping consecutive fragments j, k moves it by at
+ * most T_j alpha_j alpha_k max(1, |c_j - c_k|).
+ */
+static void decision_margins(const double* P, const double* S, const frag* buf, int cnt, double impact_min,
+                             double* mg, double* dmg) {
+  double T = 1.0, Tprev = 0.0, aprev = 0.0;
+  int prev = -1;
+  for (int k = 0; k < cnt; ++k) {
+    const frag* f = buf + k;
+    const double* r = P + (size_t)f->id * P_STRIDE;
+    const double w = T * fmin(S[S_ALPHA_MAX], r[P_OT] * f->g) * colour_scale(r);
+    if (!f->kept) {
+      if (w > impact_min) *mg = fmin(*mg, f->margin);
+      continue;
+    }
+    const double a = f->alpha;
+    const double Tn = T * (1.0 - a);
+    if (w > impact_min) *mg = fmin(*mg, fmin(f->margin, rel_margin(Tn, S[S_T_MIN])));
+    if (Tn < S[S_T_MIN]) break;
+    if (prev >= 0) {
+      const double* rp = P + (size_t)buf[prev].id * P_STRIDE;
+      double dc = 1.0;
+      for (int ch = P_R; ch <= P_B; ++ch) dc = fmax(dc, fabs(r[ch] - rp[ch]));
+      if (Tprev * aprev * a * dc > impact_min)
+        *dmg = fmin(*dmg, fabs(f->depth - buf[prev].depth) / buf[prev].depth);
+    }
+    prev = k;
+    Tprev = T;
+    aprev = a;
+    T = Tn;
+  }
+}
+
+/* drop the fragments that are not kept, preserving order; returns the new count */
+static int compact_kept(frag* buf, int cnt) {
+  int m = 0;
+  for (int k = 0; k < cnt; ++k)
+    if (buf[k].kept) buf[m++] = buf[k];
+  return m;
 }
 
 /*
@@ -431,14 +483,13 @@ static int gather_pixel(int n, const double* P, const double* S, int px, int py,
  * T *= (1 - alpha); finally C += T bg.  Returns the number of fragments blended.
  */
 static int composite(const double* P, const double* S, const frag* buf, int cnt, const double* bg,
-                     double C[3], double* Tout, double* margin) {
+                     double C[3], double* Tout) {
   double T = 1.0;
   C[0] = C[1] = C[2] = 0.0;
   int k = 0;
   for (; k < cnt; ++k) {
     const double a = buf[k].alpha;
     const double Tn = T * (1.0 - a);
-    *margin = fmin(*margin, rel_margin(Tn, S[S_T_MIN]));
     if (Tn < S[S_T_MIN]) break;
     const double* r = P + (size_t)buf[k].id * P_STRIDE;
     C[0] += T * a * r[P_R];
@@ -453,10 +504,12 @@ static int composite(const double* P, const double* S, const frag* buf, int cnt,
 
 /*
  * Render npix pixels (indices py*W + px; pix == NULL means all W*H in raster order) from the
- * records of orc_project.  img: npix x 3 (pixel-major), Tfinal, ncontrib, margin, dmargin: npix.
+ * records of orc_project.  img: npix x 3 (pixel-major), Tfinal, ncontrib, margin, dmargin: npix
+ * (decision margins of decisions whose flip could move the pixel by more than impact_min).
  */
 int orc_render(int n, const double* P, const double* cam, const double* bg, const double* S, int npix,
-               const int* pix, double* img, double* Tfinal, int* ncontrib, double* margin, double* dmargin) {
+               const int* pix, double impact_min, double* img, double* Tfinal, int* ncontrib, double* margin,
+               double* dmargin) {
   const int W = (int)cam[C_W], H = (int)cam[C_H];
   if (pix == NULL && npix != W * H) return -1;
   int err = 0;
@@ -473,8 +526,10 @@ int orc_render(int n, const double* P, const double* cam, const double* bg, cons
       const int p = pix ? pix[j] : j;
       const int px = p % W, py = p / W;
       double mg = INFINITY, dmg = INFINITY, C[3], T;
-      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg, &dmg);
-      ncontrib[j] = composite(P, S, buf, cnt, bg, C, &T, &mg);
+      int cnt = gather_pixel(n, P, S, px, py, buf);
+      decision_margins(P, S, buf, cnt, impact_min, &mg, &dmg);
+      cnt = compact_kept(buf, cnt);
+      ncontrib[j] = composite(P, S, buf, cnt, bg, C, &T);
       img[3 * j + 0] = C[0];
       img[3 * j + 1] = C[1];
       img[3 * j + 2] = C[2];
@@ -741,9 +796,9 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
       const int px = p % W, py = p / W;
       const double* gC = dL_dimg + 3 * (size_t)j;
       if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
-      double mg = INFINITY, dmg = INFINITY, C[3], T;
-      const int cnt = gather_pixel(n, P, S, px, py, buf, &mg, &dmg);
-      const int nb = composite(P, S, buf, cnt, bg, C, &T, &mg);
+      double C[3], T;
+      const int cnt = compact_kept(buf, gather_pixel(n, P, S, px, py, buf));
+      const int nb = composite(P, S, buf, cnt, bg, C, &T);
       pixel_backward(P, buf, nb, T, bg, gC, px, py, S, Tb, g2);
     }
     free(buf);

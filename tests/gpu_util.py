@@ -6,9 +6,11 @@ import numpy as np
 # GPU and the FP64 oracle; every other pixel must match to IMG_TOL.
 FLAG_MARGIN = 1e-4
 # Two fragments whose depths differ by less than this relative gap may swap order (FP32 depth is
-# good to ~1e-7 relative).
-DEPTH_MARGIN = 1e-5
+# good to ~2e-7 relative here).
+DEPTH_MARGIN = 2e-6
 IMG_TOL = 1e-4        # max-abs on rendered images
+# only decisions whose flip could move the pixel by more than this are flagged
+IMPACT_MIN = 0.5 * IMG_TOL
 GRAD_TOL = 1e-3       # relative L2 on gradients
 
 
@@ -24,7 +26,7 @@ def oracle_views(orc, g, cams, tile=(16, 16), settings=None, bg=(0, 0, 0)):
     out = []
     for cam in cams:
         P = orc.project(g, cam, tile=tile, settings=settings)
-        img, T, nc, mg, dmg = orc.render(P, cam, bg=bg, settings=settings, depth_margin=True)
+        img, T, nc, mg, dmg = orc.render(P, cam, bg=bg, settings=settings, depth_margin=True, impact_min=IMPACT_MIN)
         W, H = int(cam["W"]), int(cam["H"])
         # one flag value per pixel: below FLAG_MARGIN means "may differ"
         flag = np.minimum(mg, dmg * (FLAG_MARGIN / DEPTH_MARGIN))
