@@ -282,6 +282,45 @@ I4D_API int32_t i4d_init_heuristic(const float* xyz, const float* rgb, const flo
                                    float st_static, float opacity, float* params, void* stream);
 
 /*
+ * Learned initialisation (not in the paper: an addition that proposes the temporal scale, motion
+ * and 4D rotation the paper sets by a heuristic in Sec. 4.1 / Sec. 3.3 "Motion-Aware Gaussian").
+ *
+ * i4d_knn_features -- per pruned point, the 16 nearest other points whose voxel cells lie within
+ * +-radius cells on every axis, ordered by (squared distance, index), as features of 64 floats:
+ * offsets / voxel (48, zeros for missing slots), distance to ref_center (host float[3]), colour (3),
+ * time, neighbours found / 16, dynamic flag, zeros; knn3 (nullable): mean distance to the 3 nearest
+ * (voxel when fewer exist).  xyz (n x 3), rgb (n x 3, NULL = 0), t, flag: DEVICE; features n x 64.
+ * table_slots: power of two >= 2 n; status: I4D_ERR_CAPACITY if the table overflowed.
+ */
+I4D_API size_t i4d_knn_workspace_size(int64_t n, int64_t table_slots);
+I4D_API int32_t i4d_knn_features(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int64_t n,
+                                 float voxel, int32_t radius, const float* ref_center, float* features, float* knn3,
+                                 int64_t table_slots, int32_t* status, void* ws, size_t ws_bytes, void* stream);
+/*
+ * MLP 64 -> 64 -> 64 -> 12, GELU (exact normal CDF), bfloat16 operands, float32 accumulation (tensor
+ * cores in the forward).  weights: DEVICE float32, packed [W1 64x64 | b1 | W2 64x64 | b2 | W3 12x64 | b3]
+ * (rows = outputs), i4d_mlp_weight_count() floats.  Outputs per point: log s_t, velocity (3), q_l, q_r.
+ * i4d_mlp_grad: gradient of the mean loss w_st (log s_t - t0)^2 + w_v |v - t1:4|^2 + w_R ||R(q_l, q_r) -
+ * t4:20||_F^2 over n points (targets n x 20: log s_t, velocity, R row-major) -> grads (overwritten),
+ * loss_out (DEVICE float, nullable).
+ */
+I4D_API int64_t i4d_mlp_weight_count(void);
+I4D_API int32_t i4d_mlp_forward(const float* features, int64_t n, const float* weights, float* out, void* stream);
+I4D_API size_t i4d_mlp_grad_workspace_size(int64_t n);
+I4D_API int32_t i4d_mlp_grad(const float* features, const float* targets, int64_t n, const float* weights, float w_st,
+                             float w_v, float w_R, float* grads, float* loss_out, void* ws, size_t ws_bytes,
+                             void* stream);
+/*
+ * i4d_init_learned -- 4D Gaussians from the pruned voxels with per-point spatial scale `spatial`
+ * (e.g. knn3), and temporal log-scale and quaternions from mlp_out (n x 12); points whose proposal is
+ * not finite or degenerate fall back to the heuristic of i4d_init_heuristic (count in *fallbacks).
+ */
+I4D_API int32_t i4d_init_learned(const float* xyz, const float* rgb, const float* t, const uint8_t* flag,
+                                 const float* spatial, const float* mlp_out, int32_t n, int32_t sh_deg,
+                                 float st_dynamic, float st_static, float opacity, float* params, int32_t* fallbacks,
+                                 void* stream);
+
+/*
  * Kernel timing (host-side tracing): when enabled, every kernel the library launches is bracketed
  * by two CUDA events recorded on its stream; i4d_profile_read() waits for them and returns, per
  * kernel name, the summed device time and the launch count.  Off by default; costs two event

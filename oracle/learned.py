@@ -1,0 +1,182 @@
+"""Oracle of the learned initialisation (test infrastructure only): neighbourhood features,
+the 3-layer GELU MLP with BF16-rounded operands, its loss and its analytic backward, in float64.
+
+The paper initialises temporal scale, rotation and motion by a heuristic (Sec. 4.1, Sec. 3.3
+"Motion-Aware Gaussian"); the learned initialisation is an addition that proposes those values
+from each pruned point's voxel neighbourhood.  Definitions:
+
+features (64 per point): the 16 nearest other points among those whose voxel cell lies within
++-radius cells of the point's cell on every axis, ordered by (squared distance, index); their
+offsets (neighbour - point) / voxel (48 values, zeros for missing slots); the distance to a
+reference centre (the mean camera centre of the video); the colour (3); the time; the number of
+neighbours found / 16; the dynamic flag; zeros to 64.  The 3-NN scale is the mean distance to the
+3 nearest neighbours (the voxel edge when fewer than 3 exist).
+
+MLP: h1 = gelu(W1 bf(x) + b1), h2 = gelu(W2 bf(h1) + b2), y = W3 bf(h2) + b3 with bf() rounding to
+bfloat16 (round to nearest even) and W* rounded to bfloat16; gelu(z) = z Phi(z) with the exact
+normal CDF.  y = (log s_t, v_x, v_y, v_z, q_l (4), q_r (4)).
+
+loss (mean over points): w_st (y0 - log s_t*)^2 + w_v |v - v*|^2 + w_R ||R(q_l, q_r) - R*||_F^2 with
+R(q_l, q_r) the 4D rotation v -> q_l v q_r of the normalised quaternions (sign-free target).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+LAYER_SHAPES = [(64, 64), (64, 64), (12, 64)]
+
+
+def weight_count() -> int:
+    return sum(o * i + o for o, i in LAYER_SHAPES)
+
+
+def unpack_weights(w: np.ndarray):
+    out, off = [], 0
+    for o, i in LAYER_SHAPES:
+        W = w[off:off + o * i].reshape(o, i)
+        off += o * i
+        b = w[off:off + o]
+        off += o
+        out.append((W, b))
+    return out
+
+
+def bf16(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to bfloat16 (round to nearest, ties to even), returned as float64."""
+    a = np.ascontiguousarray(np.asarray(x, np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    rounding = 0x7FFF + ((u >> 16) & 1)
+    r = ((u + rounding) >> 16) << 16
+    r = np.where(np.isnan(a), u, r)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def knn_features(xyz, rgb, t, flag, voxel: float, ref_center, radius: int = 2, k: int = 16):
+    """Brute-force neighbourhood features of every point (O(n^2); small n only)."""
+    xyz = np.asarray(xyz, np.float64)
+    n = xyz.shape[0]
+    cell = np.floor(np.asarray(xyz, np.float32) * np.float32(1.0 / np.float32(voxel))).astype(np.int64)
+    feats = np.zeros((n, 64))
+    knn3 = np.zeros(n)
+    nbr_idx = np.full((n, k), -1, np.int64)
+    for i in range(n):
+        near = np.all(np.abs(cell - cell[i]) <= radius, axis=1)
+        near[i] = False
+        js = np.nonzero(near)[0]
+        d2 = np.sum((xyz[js] - xyz[i]) ** 2, axis=1)
+        order = np.lexsort((js, d2))
+        js, d2 = js[order][:k], d2[order][:k]
+        nbr_idx[i, :len(js)] = js
+        feats[i, :3 * len(js)] = ((xyz[js] - xyz[i]) / voxel).reshape(-1)
+        feats[i, 48] = np.linalg.norm(xyz[i] - np.asarray(ref_center, np.float64))
+        feats[i, 49:52] = rgb[i]
+        feats[i, 52] = t[i]
+        feats[i, 53] = len(js) / k
+        feats[i, 54] = float(flag[i])
+        knn3[i] = np.sqrt(d2[:3]).mean() if len(js) >= 3 else voxel
+    return feats, knn3, nbr_idx
+
+
+def forward(w: np.ndarray, x: np.ndarray):
+    """Returns (y, cache) for the backward."""
+    (W1, b1), (W2, b2), (W3, b3) = unpack_weights(np.asarray(w, np.float64))
+    W1, W2, W3 = bf16(W1), bf16(W2), bf16(W3)
+    x0 = bf16(x)
+    z1 = x0 @ W1.T + b1
+    h1 = bf16(gelu(z1))
+    z2 = h1 @ W2.T + b2
+    h2 = bf16(gelu(z2))
+    y = h2 @ W3.T + b3
+    return y, (x0, z1, h1, z2, h2, W1, W2, W3)
+
+
+def _left(p):
+    a, b, c, d = p
+    return np.array([[a, -d, c, b], [d, a, -b, c], [-c, b, a, d], [-b, -c, -d, a]])
+
+
+def _right(q):
+    e, f, g, h = q
+    return np.array([[e, h, -g, f], [-h, e, f, g], [g, -f, e, h], [-f, -g, -h, e]])
+
+
+def rotation(ql, qr):
+    """4D rotation matrix of v -> q_l v q_r (vector (x,y,z,t) <-> quaternion t + xi + yj + zk)."""
+    ql = np.asarray(ql, np.float64) / np.linalg.norm(ql)
+    qr = np.asarray(qr, np.float64) / np.linalg.norm(qr)
+    return _left(ql) @ _right(qr)
+
+
+def _rotation_grad(ql, qr, G):
+    """Gradient of <G, R(q_l, q_r)> with respect to the unnormalised quaternions: R = L(ql_hat)
+    Rr(qr_hat) is linear in each quaternion, dR/dql_hat_j = L(e_j) Rr, dR/dqr_hat_j = L Rr(e_j), then
+    through q_hat = q / |q|."""
+    nl, nr = np.linalg.norm(ql), np.linalg.norm(qr)
+    qlh, qrh = np.asarray(ql, np.float64) / nl, np.asarray(qr, np.float64) / nr
+    Lm, Rm = _left(qlh), _right(qrh)
+    E = np.eye(4)
+    gl = np.array([np.sum(G * (_left(E[j]) @ Rm)) for j in range(4)])
+    gr = np.array([np.sum(G * (Lm @ _right(E[j]))) for j in range(4)])
+    gl = (gl - qlh * (qlh @ gl)) / nl
+    gr = (gr - qrh * (qrh @ gr)) / nr
+    return gl, gr
+
+
+def loss_and_grad(y: np.ndarray, target: np.ndarray, w_st=1.0, w_v=1.0, w_R=1.0):
+    """target: (n, 20) = (log s_t, v (3), R (16, row-major)).  Returns (loss, dL/dy)."""
+    n = y.shape[0]
+    dy = np.zeros_like(y, dtype=np.float64)
+    loss = 0.0
+    for i in range(n):
+        e0 = y[i, 0] - target[i, 0]
+        ev = y[i, 1:4] - target[i, 1:4]
+        eR = rotation(y[i, 4:8], y[i, 8:12]) - target[i, 4:20].reshape(4, 4)
+        loss += w_st * e0 * e0 + w_v * ev @ ev + w_R * np.sum(eR * eR)
+        dy[i, 0] = 2 * w_st * e0
+        dy[i, 1:4] = 2 * w_v * ev
+        gl, gr = _rotation_grad(y[i, 4:8], y[i, 8:12], 2 * w_R * eR)
+        dy[i, 4:8] = gl
+        dy[i, 8:12] = gr
+    return loss / n, dy / n
+
+
+def backward(w: np.ndarray, cache, dy: np.ndarray) -> np.ndarray:
+    """Gradient of sum(dy * y) with respect to the float32 master weights (straight through the
+    bfloat16 rounding of the weights and activations), in the packed weight layout."""
+    x0, z1, h1, z2, h2, W1, W2, W3 = cache
+    dW3 = dy.T @ h2
+    db3 = dy.sum(0)
+    dh2 = dy @ W3
+    dz2 = dh2 * gelu_grad(z2)
+    dW2 = dz2.T @ h1
+    db2 = dz2.sum(0)
+    dh1 = dz2 @ W2
+    dz1 = dh1 * gelu_grad(z1)
+    dW1 = dz1.T @ x0
+    db1 = dz1.sum(0)
+    return np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
+
+
+def init_weights(seed: int) -> np.ndarray:
+    r = np.random.default_rng(seed)
+    parts = []
+    for o, i in LAYER_SHAPES:
+        parts.append(r.normal(0.0, 1.0 / math.sqrt(i), size=o * i))
+        parts.append(np.zeros(o))
+    w = np.concatenate(parts).astype(np.float32)
+    # start the quaternion heads at the identity rotation (a + 0i + 0j + 0k)
+    off = 64 * 64 + 64 + 64 * 64 + 64 + 12 * 64
+    w[off + 4] = 1.0
+    w[off + 8] = 1.0
+    return w

@@ -88,6 +88,14 @@ _SIGS = {
     "i4d_render_bwd_noalloc": (c_i32, [ctypes.POINTER(Gaussians), ctypes.POINTER(Views), c_vp,
                                        ctypes.POINTER(Settings), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                        c_vp]),
+    "i4d_knn_workspace_size": (c_sz, [c_i64, c_i64]),
+    "i4d_knn_features": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f, c_i32, ctypes.POINTER(c_f), c_vp, c_vp, c_i64,
+                                 c_vp, c_vp, c_sz, c_vp]),
+    "i4d_mlp_weight_count": (c_i64, []),
+    "i4d_mlp_forward": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "i4d_mlp_grad_workspace_size": (c_sz, [c_i64]),
+    "i4d_mlp_grad": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_f, c_f, c_f, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "i4d_init_learned": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_f, c_f, c_f, c_vp, c_vp, c_vp]),
     "i4d_profile_enable": (c_i32, [c_i32]),
     "i4d_profile_reset": (None, []),
     "i4d_profile_count": (c_i32, []),
@@ -268,3 +276,41 @@ def i4d_render_bwd_noalloc(g: Gaussians, views: Views, cams, settings, proj, tou
         raise I4DError(f"i4d_render_bwd_noalloc: n_views * n = {views.n_views * g.n} exceeds the fixed scratch of "
                        f"{int(lib.i4d_render_bwd_noalloc_max_records())} records")
     check(rc, "i4d_render_bwd_noalloc")
+
+
+def i4d_knn_workspace_size(n: int, table_slots: int) -> int:
+    return int(load().i4d_knn_workspace_size(int(n), int(table_slots)))
+
+
+def i4d_knn_features(xyz, rgb, t, flag, voxel, radius, ref_center, features, knn3, table_slots, status, ws,
+                     stream=None):
+    ref = (c_f * 3)(*[float(x) for x in ref_center])
+    check(load().i4d_knn_features(ptr(xyz), ptr(rgb), ptr(t), ptr(flag), xyz.shape[0], float(voxel), int(radius), ref,
+                                  ptr(features), ptr(knn3), int(table_slots), ptr(status), ptr(ws),
+                                  ws.numel() * ws.element_size(), stream_ptr(stream)), "i4d_knn_features")
+
+
+def i4d_mlp_weight_count() -> int:
+    return int(load().i4d_mlp_weight_count())
+
+
+def i4d_mlp_forward(features, weights, out, stream=None):
+    check(load().i4d_mlp_forward(ptr(features), features.shape[0], ptr(weights), ptr(out), stream_ptr(stream)),
+          "i4d_mlp_forward")
+
+
+def i4d_mlp_grad_workspace_size(n: int) -> int:
+    return int(load().i4d_mlp_grad_workspace_size(int(n)))
+
+
+def i4d_mlp_grad(features, targets, weights, w_st, w_v, w_R, grads, loss_out, ws, stream=None):
+    check(load().i4d_mlp_grad(ptr(features), ptr(targets), features.shape[0], ptr(weights), float(w_st), float(w_v),
+                              float(w_R), ptr(grads), ptr(loss_out), ptr(ws), ws.numel() * ws.element_size(),
+                              stream_ptr(stream)), "i4d_mlp_grad")
+
+
+def i4d_init_learned(xyz, rgb, t, flag, spatial, mlp_out, n, sh_deg, st_dynamic, st_static, opacity, params,
+                     fallbacks, stream=None):
+    check(load().i4d_init_learned(ptr(xyz), ptr(rgb), ptr(t), ptr(flag), ptr(spatial), ptr(mlp_out), int(n),
+                                  int(sh_deg), float(st_dynamic), float(st_static), float(opacity), ptr(params),
+                                  ptr(fallbacks), stream_ptr(stream)), "i4d_init_learned")

@@ -227,6 +227,52 @@ int32_t i4d_init_heuristic(const float* xyz, const float* rgb, const float* t, c
                                            opacity, params, (cudaStream_t)stream));
 }
 
+int32_t i4d_init_learned(const float* xyz, const float* rgb, const float* t, const uint8_t* flag,
+                         const float* spatial, const float* mlp_out, int32_t n, int32_t sh_deg, float st_dynamic,
+                         float st_static, float opacity, float* params, int32_t* fallbacks, void* stream) {
+  if (n < 0 || sh_deg < 0 || sh_deg > 3 || !(st_dynamic > 0.0f) || !(st_static > 0.0f) ||
+      !(opacity > 0.0f && opacity < 1.0f))
+    return I4D_ERR_ARG;
+  if (n > 0 && (!xyz || !spatial || !mlp_out || !params || !aligned16(params))) return I4D_ERR_ARG;
+  return cuda_status(launch_init_learned(xyz, rgb, t, flag, spatial, mlp_out, n, sh_deg, st_dynamic, st_static,
+                                         opacity, params, fallbacks, (cudaStream_t)stream));
+}
+
+size_t i4d_knn_workspace_size(int64_t n, int64_t table_slots) {
+  if (n < 0 || table_slots < 1 || (table_slots & (table_slots - 1))) return 0;
+  return knn_workspace_bytes(n, table_slots);
+}
+
+int32_t i4d_knn_features(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int64_t n,
+                         float voxel, int32_t radius, const float* ref_center, float* features, float* knn3,
+                         int64_t table_slots, int32_t* status, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 0 || n >= (1ll << 32) - 1 || !(voxel > 0.0f) || radius < 0 || radius > 4 || !ref_center || !status ||
+      table_slots < 1 || (table_slots & (table_slots - 1)))
+    return I4D_ERR_ARG;
+  if (n > 0 && (!xyz || !features || !ws)) return I4D_ERR_ARG;
+  if (ws_bytes < knn_workspace_bytes(n, table_slots)) return I4D_ERR_WORKSPACE;
+  return cuda_status(launch_knn_features(xyz, rgb, t, flag, n, voxel, radius, ref_center, features, knn3, table_slots,
+                                         status, ws, (cudaStream_t)stream));
+}
+
+int64_t i4d_mlp_weight_count(void) { return mlp_weight_count(); }
+
+int32_t i4d_mlp_forward(const float* features, int64_t n, const float* weights, float* out, void* stream) {
+  if (n < 0 || (n > 0 && (!features || !weights || !out))) return I4D_ERR_ARG;
+  return cuda_status(launch_mlp_forward(features, n, weights, out, (cudaStream_t)stream));
+}
+
+size_t i4d_mlp_grad_workspace_size(int64_t n) { return n < 0 ? 0 : mlp_grad_workspace_bytes(n); }
+
+int32_t i4d_mlp_grad(const float* features, const float* targets, int64_t n, const float* weights, float w_st,
+                     float w_v, float w_R, float* grads, float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 0 || !weights || !grads || !ws) return I4D_ERR_ARG;
+  if (n > 0 && (!features || !targets)) return I4D_ERR_ARG;
+  if (ws_bytes < mlp_grad_workspace_bytes(n)) return I4D_ERR_WORKSPACE;
+  return cuda_status(
+      launch_mlp_grad(features, targets, n, weights, w_st, w_v, w_R, grads, loss_out, ws, (cudaStream_t)stream));
+}
+
 size_t i4d_prune_workspace_size(int64_t n_points, int64_t table_slots) {
   if (n_points < 0 || table_slots < 1 || (table_slots & (table_slots - 1))) return 0;
   return prune_workspace_bytes(n_points, table_slots);

@@ -74,4 +74,19 @@ cudaError_t launch_init_heuristic(const float* xyz, const float* rgb, const floa
                                   int sh_deg, float spatial_scale, float st_dynamic, float st_static, float opacity,
                                   float* params, cudaStream_t st);
 
+cudaError_t launch_init_learned(const float* xyz, const float* rgb, const float* t, const uint8_t* flag,
+                                const float* spatial, const float* y, int n, int sh_deg, float st_dynamic,
+                                float st_static, float opacity, float* params, int32_t* fallbacks, cudaStream_t st);
+
+// neighbourhood features and the learned-initialisation MLP
+size_t knn_workspace_bytes(int64_t n, int64_t slots);
+cudaError_t launch_knn_features(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int64_t n,
+                                float voxel, int radius, const float* ref, float* feat, float* knn3, int64_t slots,
+                                int32_t* status, void* ws, cudaStream_t st);
+int64_t mlp_weight_count();
+size_t mlp_grad_workspace_bytes(int64_t n);
+cudaError_t launch_mlp_forward(const float* feat, int64_t n, const float* w, float* out, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* feat, const float* tgt, int64_t n, const float* w, float w_st, float w_v,
+                            float w_R, float* grads, float* loss, void* ws, cudaStream_t st);
+
 }  // namespace i4d

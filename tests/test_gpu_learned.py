@@ -1,0 +1,128 @@
+"""GPU <-> oracle parity of the learned initialisation: neighbourhood features, the BF16 MLP
+forward (tensor cores) and its loss gradient with respect to the weights, through the C ABI."""
+import numpy as np
+import pytest
+
+from gpu_util import GRAD_TOL, rel_l2
+from oracle import learned as OL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    from paper_2510_01119_gb300 import build, _lib
+    build.build()
+    _lib.load()
+    assert torch.cuda.is_available()
+    return torch.device("cuda:0")
+
+
+def _cloud(seed, n):
+    r = np.random.default_rng(seed)
+    # clustered points on a few planes, like pruned voxel centroids of walls and objects
+    k = r.integers(0, 4, n)
+    base = r.uniform(-0.3, 0.3, size=(n, 3))
+    base[np.arange(n), k % 3] = 0.05 * k - 0.1
+    xyz = (base + r.normal(0, 0.004, size=(n, 3))).astype(np.float32)
+    return xyz, r.uniform(size=(n, 3)).astype(np.float32), r.uniform(size=n).astype(np.float32), \
+        (r.uniform(size=n) < 0.3).astype(np.uint8)
+
+
+def _t(a, dev):
+    import torch
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def test_knn_features_match_oracle(dev):
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    n, voxel = 3000, 0.02
+    xyz, rgb, t, flag = _cloud(1, n)
+    slots = 1 << 14
+    feats = torch.zeros(n, 64, device=dev)
+    knn3 = torch.zeros(n, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(L.i4d_knn_workspace_size(n, slots), dtype=torch.uint8, device=dev)
+    L.i4d_knn_features(_t(xyz, dev), _t(rgb, dev), _t(t, dev), _t(flag, dev), voxel, 2, (0.1, -0.2, -3.0), feats,
+                       knn3, slots, status, ws)
+    assert int(status.item()) == 0
+    want, want3, idx = OL.knn_features(xyz, rgb, t, flag, voxel, (0.1, -0.2, -3.0), radius=2)
+    got = feats.cpu().numpy()
+    # rows whose ordering could flip: two of the first 17 squared distances within 1e-5 relative
+    x64 = xyz.astype(np.float64)
+    tie = np.zeros(n, bool)
+    for i in range(n):
+        js = idx[i][idx[i] >= 0]
+        d = np.sort(np.sum((x64[js] - x64[i]) ** 2, axis=1))
+        tie[i] = len(d) > 1 and np.any(np.diff(d) <= 1e-5 * d[1:])
+    ok = ~tie
+    assert ok.sum() > 0.95 * n
+    assert np.abs(got[ok] - want[ok]).max() < 2e-4
+    assert np.allclose(knn3.cpu().numpy()[ok], want3[ok], rtol=1e-5)
+    assert np.abs(got[:, 48:] - want[:, 48:]).max() < 1e-5
+
+
+def test_mlp_forward_matches_oracle(dev):
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    r = np.random.default_rng(2)
+    n = 1003                                   # not a multiple of the 64-point chunk
+    w = (OL.init_weights(7) + r.normal(0, 0.02, OL.weight_count())).astype(np.float32)
+    x = np.concatenate([r.normal(0, 1.2, (n, 48)), r.uniform(2, 4, (n, 1)), r.uniform(size=(n, 5)),
+                        np.zeros((n, 10))], axis=1).astype(np.float32)
+    assert L.i4d_mlp_weight_count() == OL.weight_count()
+    out = torch.zeros(n, 12, device=dev)
+    L.i4d_mlp_forward(_t(x, dev), _t(w, dev), out)
+    want, _ = OL.forward(w, x)
+    err = np.abs(out.cpu().numpy() - want)
+    # a hidden activation that lands on a bf16 rounding boundary can round the other way in float32
+    assert np.quantile(err, 0.99) < 1e-4
+    assert err.max() < 5e-3
+
+
+def test_mlp_weight_gradient_matches_oracle(dev):
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    r = np.random.default_rng(3)
+    n = 777
+    w = (OL.init_weights(9) + r.normal(0, 0.02, OL.weight_count())).astype(np.float32)
+    x = np.concatenate([r.normal(0, 1.0, (n, 48)), r.uniform(2, 4, (n, 1)), r.uniform(size=(n, 5)),
+                        np.zeros((n, 10))], axis=1).astype(np.float32)
+    tgt = np.zeros((n, 20), np.float32)
+    tgt[:, 0] = r.normal(-2, 1, n)
+    tgt[:, 1:4] = r.normal(0, 0.3, (n, 3))
+    for i in range(n):
+        tgt[i, 4:] = OL.rotation(r.normal(size=4), r.normal(size=4)).ravel()
+    grads = torch.zeros(OL.weight_count(), device=dev)
+    loss = torch.zeros(1, device=dev)
+    ws = torch.empty(L.i4d_mlp_grad_workspace_size(n), dtype=torch.uint8, device=dev)
+    L.i4d_mlp_grad(_t(x, dev), _t(tgt, dev), _t(w, dev), 1.0, 2.0, 0.5, grads, loss, ws)
+    y, cache = OL.forward(w, x)
+    want_loss, dy = OL.loss_and_grad(y, tgt.astype(np.float64), 1.0, 2.0, 0.5)
+    want = OL.backward(w, cache, dy)
+    assert float(loss.item()) == pytest.approx(want_loss, rel=1e-4)
+    assert rel_l2(grads.cpu().numpy(), want) < GRAD_TOL
+
+
+def test_init_learned_falls_back_on_degenerate_proposals(dev):
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    n = 5
+    xyz = np.arange(15, dtype=np.float32).reshape(5, 3)
+    y = np.zeros((n, 12), np.float32)
+    y[:, 0] = -3.0
+    y[:, 4] = y[:, 8] = 1.0
+    y[1, 4:8] = 0.0            # zero quaternion
+    y[2, 0] = np.nan           # not finite
+    flag = np.array([0, 1, 0, 1, 0], np.uint8)
+    params = torch.zeros(5 * n * 4, device=dev)
+    fb = torch.zeros(1, dtype=torch.int32, device=dev)
+    L.i4d_init_learned(_t(xyz, dev), None, None, _t(flag, dev), _t(np.full(n, 0.01, np.float32), dev), _t(y, dev), n,
+                       0, 0.01, 1.0, 0.1, params, fb)
+    P = params.cpu().numpy().reshape(5, n, 4)
+    assert int(fb.item()) == 2
+    assert P[1, 0, 3] == pytest.approx(-3.0) and P[1, 1, 3] == pytest.approx(np.log(0.01))
+    assert P[1, 2, 3] == pytest.approx(0.0) and np.allclose(P[2, 1], [1, 0, 0, 0])
+    assert np.allclose(P[0, :, :3], xyz) and np.allclose(P[1, :, 0], np.log(0.01))
