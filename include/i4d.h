@@ -304,6 +304,9 @@ I4D_API int32_t i4d_knn_features(const float* xyz, const float* rgb, const float
  * t4:20||_F^2 over n points (targets n x 20: log s_t, velocity, R row-major) -> grads (overwritten),
  * loss_out (DEVICE float, nullable).
  */
+/* i4d_motion_targets -- per Gaussian (log s_t, velocity b/c of Eq. 7, R row-major): n x 20 floats,
+ * the training targets of the MLP when taken from Gaussians fitted by the plain method. */
+I4D_API int32_t i4d_motion_targets(const i4d_gaussians* g, float* out, void* stream);
 I4D_API int64_t i4d_mlp_weight_count(void);
 I4D_API int32_t i4d_mlp_forward(const float* features, int64_t n, const float* weights, float* out, void* stream);
 I4D_API size_t i4d_mlp_grad_workspace_size(int64_t n);
@@ -314,6 +317,7 @@ I4D_API int32_t i4d_mlp_grad(const float* features, const float* targets, int64_
  * i4d_init_learned -- 4D Gaussians from the pruned voxels with per-point spatial scale `spatial`
  * (e.g. knn3), and temporal log-scale and quaternions from mlp_out (n x 12); points whose proposal is
  * not finite or degenerate fall back to the heuristic of i4d_init_heuristic (count in *fallbacks).
+ * mlp_out NULL: the heuristic for every point (with the per-point spatial scale).
  */
 I4D_API int32_t i4d_init_learned(const float* xyz, const float* rgb, const float* t, const uint8_t* flag,
                                  const float* spatial, const float* mlp_out, int32_t n, int32_t sh_deg,

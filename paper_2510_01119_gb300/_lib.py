@@ -91,6 +91,7 @@ _SIGS = {
     "i4d_knn_workspace_size": (c_sz, [c_i64, c_i64]),
     "i4d_knn_features": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f, c_i32, ctypes.POINTER(c_f), c_vp, c_vp, c_i64,
                                  c_vp, c_vp, c_sz, c_vp]),
+    "i4d_motion_targets": (c_i32, [ctypes.POINTER(Gaussians), c_vp, c_vp]),
     "i4d_mlp_weight_count": (c_i64, []),
     "i4d_mlp_forward": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "i4d_mlp_grad_workspace_size": (c_sz, [c_i64]),
@@ -314,3 +315,7 @@ def i4d_init_learned(xyz, rgb, t, flag, spatial, mlp_out, n, sh_deg, st_dynamic,
     check(load().i4d_init_learned(ptr(xyz), ptr(rgb), ptr(t), ptr(flag), ptr(spatial), ptr(mlp_out), int(n),
                                   int(sh_deg), float(st_dynamic), float(st_static), float(opacity), ptr(params),
                                   ptr(fallbacks), stream_ptr(stream)), "i4d_init_learned")
+
+
+def i4d_motion_targets(g: Gaussians, out, stream=None):
+    check(load().i4d_motion_targets(ctypes.byref(g), ptr(out), stream_ptr(stream)), "i4d_motion_targets")

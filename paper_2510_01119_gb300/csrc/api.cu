@@ -233,7 +233,7 @@ int32_t i4d_init_learned(const float* xyz, const float* rgb, const float* t, con
   if (n < 0 || sh_deg < 0 || sh_deg > 3 || !(st_dynamic > 0.0f) || !(st_static > 0.0f) ||
       !(opacity > 0.0f && opacity < 1.0f))
     return I4D_ERR_ARG;
-  if (n > 0 && (!xyz || !spatial || !mlp_out || !params || !aligned16(params))) return I4D_ERR_ARG;
+  if (n > 0 && (!xyz || !spatial || !params || !aligned16(params))) return I4D_ERR_ARG;
   return cuda_status(launch_init_learned(xyz, rgb, t, flag, spatial, mlp_out, n, sh_deg, st_dynamic, st_static,
                                          opacity, params, fallbacks, (cudaStream_t)stream));
 }
@@ -253,6 +253,12 @@ int32_t i4d_knn_features(const float* xyz, const float* rgb, const float* t, con
   if (ws_bytes < knn_workspace_bytes(n, table_slots)) return I4D_ERR_WORKSPACE;
   return cuda_status(launch_knn_features(xyz, rgb, t, flag, n, voxel, radius, ref_center, features, knn3, table_slots,
                                          status, ws, (cudaStream_t)stream));
+}
+
+int32_t i4d_motion_targets(const i4d_gaussians* g, float* out, void* stream) {
+  if (!g || g->n < 0 || g->sh_deg < 0 || g->sh_deg > 3 || g->mode < 0 || g->mode > 2) return I4D_ERR_ARG;
+  if (g->n > 0 && (!g->params || !out || !aligned16(g->params))) return I4D_ERR_ARG;
+  return cuda_status(launch_motion_targets(g->params, g->n, g->mode, out, (cudaStream_t)stream));
 }
 
 int64_t i4d_mlp_weight_count(void) { return mlp_weight_count(); }

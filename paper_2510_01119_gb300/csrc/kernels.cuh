@@ -78,6 +78,8 @@ cudaError_t launch_init_learned(const float* xyz, const float* rgb, const float*
                                 const float* spatial, const float* y, int n, int sh_deg, float st_dynamic,
                                 float st_static, float opacity, float* params, int32_t* fallbacks, cudaStream_t st);
 
+cudaError_t launch_motion_targets(const float* params, int n, int mode, float* out, cudaStream_t st);
+
 // neighbourhood features and the learned-initialisation MLP
 size_t knn_workspace_bytes(int64_t n, int64_t slots);
 cudaError_t launch_knn_features(const float* xyz, const float* rgb, const float* t, const uint8_t* flag, int64_t n,
