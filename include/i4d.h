@@ -288,7 +288,9 @@ I4D_API int32_t i4d_init_heuristic(const float* xyz, const float* rgb, const flo
  * i4d_knn_features -- per pruned point, the 16 nearest other points whose voxel cells lie within
  * +-radius cells on every axis, ordered by (squared distance, index), as features of 64 floats:
  * offsets / voxel (48, zeros for missing slots), distance to ref_center (host float[3]), colour (3),
- * time, neighbours found / 16, dynamic flag, zeros; knn3 (nullable): mean distance to the 3 nearest
+ * time, neighbours found / 16, dynamic flag, the neighbourhood's least-squares velocity
+ * sum dt o / (sum dt^2 + 1e-6) / 16 (3; dt = neighbour time - point time, o = offset in voxels), the
+ * RMS of dt, zeros; knn3 (nullable): mean distance to the 3 nearest
  * (voxel when fewer exist).  xyz (n x 3), rgb (n x 3, NULL = 0), t, flag: DEVICE; features n x 64.
  * table_slots: power of two >= 2 n; status: I4D_ERR_CAPACITY if the table overflowed.
  */

@@ -9,7 +9,9 @@ features (64 per point): the 16 nearest other points among those whose voxel cel
 +-radius cells of the point's cell on every axis, ordered by (squared distance, index); their
 offsets (neighbour - point) / voxel (48 values, zeros for missing slots); the distance to a
 reference centre (the mean camera centre of the video); the colour (3); the time; the number of
-neighbours found / 16; the dynamic flag; zeros to 64.  The 3-NN scale is the mean distance to the
+neighbours found / 16; the dynamic flag; the least-squares velocity of the neighbourhood,
+sum_k dt_k o_k / (sum_k dt_k^2 + 1e-6) with o_k the offsets in voxels and dt_k the neighbours' time
+minus the point's, divided by 16 (3); the RMS of dt_k (1); zeros to 64.  The 3-NN scale is the mean distance to the
 3 nearest neighbours (the voxel edge when fewer than 3 exist).
 
 MLP: h1 = gelu(W1 bf(x) + b1), h2 = gelu(W2 bf(h1) + b2), y = W3 bf(h2) + b3 with bf() rounding to
@@ -84,6 +86,11 @@ def knn_features(xyz, rgb, t, flag, voxel: float, ref_center, radius: int = 2, k
         feats[i, 52] = t[i]
         feats[i, 53] = len(js) / k
         feats[i, 54] = float(flag[i])
+        if len(js):
+            dt = np.asarray(t, np.float64)[js] - float(t[i])
+            o = (xyz[js] - xyz[i]) / voxel
+            feats[i, 55:58] = (dt[:, None] * o).sum(0) / (np.sum(dt * dt) + 1e-6) / 16.0
+            feats[i, 58] = math.sqrt(np.mean(dt * dt))
         knn3[i] = np.sqrt(d2[:3]).mean() if len(js) >= 3 else voxel
     return feats, knn3, nbr_idx
 

@@ -132,14 +132,24 @@ __global__ void __launch_bounds__(128) knn_query(const float* __restrict__ xyz, 
   float* f = feat + 64 * i;
   int found = 0;
   const float iv = 1.0f / voxel;
+  const float ti = t ? t[i] : 0.0f;
+  float vx = 0.f, vy = 0.f, vz = 0.f, dtt = 0.f;  // least-squares velocity of the neighbourhood
 #pragma unroll
   for (int k = 0; k < kK; ++k) {
     const bool ok = bj[k] != kEnd;
     found += ok ? 1 : 0;
     const int64_t j = ok ? (int64_t)bj[k] : i;
-    f[3 * k] = ok ? (xyz[3 * j] - px) * iv : 0.0f;
-    f[3 * k + 1] = ok ? (xyz[3 * j + 1] - py) * iv : 0.0f;
-    f[3 * k + 2] = ok ? (xyz[3 * j + 2] - pz) * iv : 0.0f;
+    const float ox = ok ? (xyz[3 * j] - px) * iv : 0.0f;
+    const float oy = ok ? (xyz[3 * j + 1] - py) * iv : 0.0f;
+    const float oz = ok ? (xyz[3 * j + 2] - pz) * iv : 0.0f;
+    f[3 * k] = ox;
+    f[3 * k + 1] = oy;
+    f[3 * k + 2] = oz;
+    const float dt = (ok && t) ? t[j] - ti : 0.0f;
+    vx += dt * ox;
+    vy += dt * oy;
+    vz += dt * oz;
+    dtt += dt * dt;
   }
   const float ex = px - rx, ey = py - ry, ez = pz - rz;
   f[48] = sqrtf(ex * ex + ey * ey + ez * ez);
@@ -149,8 +159,13 @@ __global__ void __launch_bounds__(128) knn_query(const float* __restrict__ xyz, 
   f[52] = t ? t[i] : 0.0f;
   f[53] = (float)found / (float)kK;
   f[54] = flag ? (float)(flag[i] != 0) : 0.0f;
+  const float iv16 = 1.0f / (16.0f * (dtt + 1e-6f));
+  f[55] = vx * iv16;
+  f[56] = vy * iv16;
+  f[57] = vz * iv16;
+  f[58] = found ? sqrtf(dtt / (float)found) : 0.0f;
 #pragma unroll
-  for (int k = 55; k < 64; ++k) f[k] = 0.0f;
+  for (int k = 59; k < 64; ++k) f[k] = 0.0f;
   if (knn3) knn3[i] = found >= 3 ? (sqrtf(bd[0]) + sqrtf(bd[1]) + sqrtf(bd[2])) * (1.0f / 3.0f) : voxel;
 }
 
