@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--eager", action="store_true", help="launch the step eagerly instead of a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--tile", default="auto", help="screen tile WxH, or auto (time the candidates)")
     ap.add_argument("--small", action="store_true",
                     help="50-frame video (~0.4 M Gaussians) for profiler captures; not a bench value")
     return ap.parse_args()
@@ -178,9 +179,23 @@ def build_gpu_workload(dev, vid):
     n = int(out["n_kept"].item())
     params = torch.empty(5 * n * 4, dtype=torch.float32, device=dev)
     st_dyn, st_static = T.temporal_scales(N_FRAMES)
-    L.i4d_init_heuristic(out["xyz"], out["rgb"], out["t"], out["flag"], n, 0, T.scale_for_voxel(synth.PRUNE_VOXEL),
-                         st_dyn, st_static, 0.1, params)
-    del pr, depth, rgb, dyn
+    # heuristic initialisation with the per-point spatial scale of standard 3D splatting (mean
+    # distance to the 3 nearest pruned points), computed by the neighbourhood kernel
+    slots = 1
+    while slots < 2 * n:
+        slots <<= 1
+    feats = torch.empty(n, 64, device=dev)
+    knn3 = torch.empty(n, device=dev)
+    kst = torch.zeros(1, dtype=torch.int32, device=dev)
+    kws = torch.empty(L.i4d_knn_workspace_size(n, slots), dtype=torch.uint8, device=dev)
+    ref = np.mean([-np.asarray(c["R"], np.float64).T @ np.asarray(c["t"], np.float64) for c in vid["cams"]], axis=0)
+    L.i4d_knn_features(out["xyz"][:n], out["rgb"][:n], out["t"][:n], out["flag"][:n], synth.PRUNE_VOXEL, 2, ref, feats,
+                       knn3, slots, kst, kws)
+    L.i4d_init_learned(out["xyz"], out["rgb"], out["t"], out["flag"], knn3, None, n, 0, st_dyn, st_static, 0.1,
+                       params, None)
+    if int(kst.item()) != 0:
+        raise RuntimeError("neighbour table overflowed")
+    del pr, depth, rgb, dyn, feats, kws
     # target bank: the hidden scene rendered at every frame of the arc, at both resolutions
     hidden = synth.room_gaussians(1003, 200000)
     hp = R.pack_params(hidden, dev)
@@ -279,7 +294,9 @@ def oracle_workload(vid):
     res = oracle.prune(pts, synth.PRUNE_VOXEL, synth.PRUNE_VOXEL, synth.PRUNE_MIN_SUPPORT, rgb=rgb, t=t,
                        dyn=vid["dyn"].reshape(-1))
     prune_s = time.perf_counter() - t0
-    g = oracle.init_heuristic(res, 0.5 * synth.PRUNE_VOXEL, 2.0 / (N_FRAMES - 1), 1.0)
+    from oracle import learned as OL
+    knn3 = OL.knn3_scale(res["centroid"].astype(np.float32), synth.PRUNE_VOXEL, radius=2)
+    g = oracle.init_heuristic(res, knn3, 2.0 / (N_FRAMES - 1), 1.0)
     return g, prune_s
 
 
@@ -362,9 +379,18 @@ def run_ours(args, ws, rank, local):
     sizes = T.sizes_for_batch(FULL, HALF, N_FULL, N_HALF)
     V = len(sizes)
     total_steps = args.warmup + args.steps
-    step = T.TrainStep(wl["params"], n, 0, 0, sizes, steps=max(total_steps, 2000), loss_kind=L.LOSS_L1,
-                       capacity=16 * n)
     batches = step_batches(total_steps + args.profile_steps)
+    tune = None
+    if args.tile == "auto":
+        from paper_2510_01119_gb300 import autotune
+        fa, fb = batches[0]
+        cams0 = torch.cat([wl["cam_bank"][FULL][torch.as_tensor(fa)], wl["cam_bank"][HALF][torch.as_tensor(fb)]])
+        tgt0 = torch.cat([wl["bank"][FULL][torch.as_tensor(fa)].reshape(-1), wl["bank"][HALF][torch.as_tensor(fb)].reshape(-1)])
+        tile, tune = autotune.tune_tile(wl["params"], n, sizes, cams0, tgt0)
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
+    step = T.TrainStep(wl["params"], n, 0, 0, sizes, steps=max(total_steps, 2000), loss_kind=L.LOSS_L1,
+                       capacity=16 * n, tile=tile)
     fullpix, halfpix = 3 * FULL[0] * FULL[1], 3 * HALF[0] * HALF[1]
     tgt_full = step.target[:N_FULL * fullpix].view(N_FULL, fullpix)
     tgt_half = step.target[N_FULL * fullpix:].view(N_HALF, halfpix)
@@ -470,7 +496,9 @@ def run_ours(args, ws, rank, local):
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded room depth video + hidden 4D Gaussian scene; no dataset)",
         "config": {"workload": "train_step_1M_8views", "n_gaussians": n, "n_dynamic": wl["n_dynamic"],
-                   "views": "4x960x540+4x480x270", "tile": "16x16", "loss": "L1",
+                   "views": "4x960x540+4x480x270", "tile": f"{tile[0]}x{tile[1]}",
+                   "tile_ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tune.items()} if tune else None,
+                   "init": "heuristic, 3-NN spatial scale", "loss": "L1",
                    "graph": not args.eager, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (params 90 MB + records 430 MB + bins per step)",
                    "instances": I, "visible_records": R_vis, "pixels": P},

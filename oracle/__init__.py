@@ -238,7 +238,7 @@ def cov4(logscale4, ql, qr, mode: int = MODE_FULL) -> np.ndarray:
     return out.reshape(4, 4)
 
 
-def init_heuristic(pruned: dict, spatial_scale: float, st_dynamic: float, st_static: float = 1.0,
+def init_heuristic(pruned: dict, spatial_scale, st_dynamic: float, st_static: float = 1.0,
                    opacity: float = 0.1) -> dict:
     """4D Gaussians from pruned voxels (Sec. 4.1; Sec. 3.3 "Motion-Aware Gaussian"): mean = (centroid,
     mean time); s_t = st_dynamic for dynamic voxels, st_static for static ones; isotropic spatial
@@ -246,7 +246,7 @@ def init_heuristic(pruned: dict, spatial_scale: float, st_dynamic: float, st_sta
     n = len(pruned["rep"])
     mean4 = np.c_[pruned["centroid"], pruned["t"]]
     ls = np.zeros((n, 4))
-    ls[:, :3] = np.log(spatial_scale)
+    ls[:, :3] = np.log(np.asarray(spatial_scale, np.float64)).reshape(-1, 1)
     ls[:, 3] = np.where(pruned["flag"] != 0, np.log(st_dynamic), np.log(st_static))
     q = np.zeros((n, 4))
     q[:, 0] = 1.0

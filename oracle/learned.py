@@ -95,6 +95,37 @@ def knn_features(xyz, rgb, t, flag, voxel: float, ref_center, radius: int = 2, k
     return feats, knn3, nbr_idx
 
 
+def knn3_scale(xyz, voxel: float, radius: int = 2, k0: int = 16) -> np.ndarray:
+    """The 3-NN spatial scale of every point (same definition as knn_features' second output) for
+    large point sets: candidates in distance order from a k-d tree, filtered to the +-radius cell
+    window, the first 3 survivors averaged; the query widens for points whose candidates ran out."""
+    from scipy.spatial import cKDTree
+    x64 = np.asarray(xyz, np.float64)
+    n = x64.shape[0]
+    cell = np.floor(np.asarray(xyz, np.float32) * np.float32(1.0 / np.float32(voxel))).astype(np.int64)
+    tree = cKDTree(x64)
+    out = np.full(n, float(voxel))
+    todo = np.arange(n)
+    k = k0
+    while len(todo):
+        kk = min(k, n)
+        d, j = tree.query(x64[todo], k=kk, workers=-1)
+        d, j = d.reshape(len(todo), kk), j.reshape(len(todo), kk)
+        ok = (j != todo[:, None]) & np.all(np.abs(cell[j] - cell[todo][:, None, :]) <= radius, axis=2)
+        # ties in distance are ordered by index, as in the brute-force definition
+        order = np.lexsort((j, d), axis=1)
+        d, ok = np.take_along_axis(d, order, 1), np.take_along_axis(ok, order, 1)
+        cnt = np.cumsum(ok, axis=1)
+        three = cnt[:, -1] >= 3
+        first3 = ok & (cnt <= 3)
+        s = np.where(first3, d, 0.0).sum(axis=1)
+        out[todo[three]] = s[three] / 3.0
+        done = three | (kk >= n)
+        todo = todo[~done]
+        k *= 4
+    return out
+
+
 def forward(w: np.ndarray, x: np.ndarray):
     """Returns (y, cache) for the backward."""
     (W1, b1), (W2, b2), (W3, b3) = unpack_weights(np.asarray(w, np.float64))

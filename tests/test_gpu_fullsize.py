@@ -60,6 +60,23 @@ def _sampled_parity(orc, g, cams, n_pix, seed, dev, grad_keys, min_checked=0.8):
     return checked
 
 
+def _gpu_knn3_matches(xyz, want, dev):
+    """The neighbourhood kernel's 3-NN scale over all ~1.13M kept points equals the oracle's."""
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    n = xyz.shape[0]
+    slots = 1 << int(np.ceil(np.log2(2 * n)))
+    x = torch.from_numpy(xyz).to(dev)
+    feats = torch.empty(n, 64, device=dev)
+    knn3 = torch.empty(n, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(L.i4d_knn_workspace_size(n, slots), dtype=torch.uint8, device=dev)
+    L.i4d_knn_features(x, None, None, None, synth.PRUNE_VOXEL, 2, (0.0, 0.0, 0.0), feats, knn3, slots, status, ws)
+    assert int(status.item()) == 0
+    np.testing.assert_allclose(knn3.cpu().numpy(), want, rtol=2e-6, atol=0)
+    del feats, ws
+
+
 def test_surfaces_200k_sh3_960x540_sampled(dev, orc):
     """The 200k-Gaussian surfaces workload (SH degree 3) in one 960x540 arc view."""
     g = synth.gaussians_surfaces(1)
@@ -76,11 +93,17 @@ def test_training_batch_1M_eight_views_sampled(dev, orc):
                     rgb=vid["rgb"].reshape(-1, 3).astype(np.float32) / 255.0,
                     t=np.repeat(vid["times"], 640 * 360).astype(np.float32), dyn=vid["dyn"].reshape(-1))
     del pts, vid
-    g = orc.init_heuristic(res, 0.5 * synth.PRUNE_VOXEL, 2.0 / 199, 1.0)
+    # the bench's initialisation: per-point spatial scale = mean distance to the 3 nearest kept points
+    from oracle import learned as OL
+    xyz = res["centroid"].astype(np.float32)
+    knn3 = OL.knn3_scale(xyz, synth.PRUNE_VOXEL, radius=2)
+    _gpu_knn3_matches(xyz, knn3, dev)
+    g = orc.init_heuristic(res, knn3, 2.0 / 199, 1.0)
     g = {k: (v.astype(np.float32) if isinstance(v, np.ndarray) else v) for k, v in g.items()}
     frames = [3, 61, 122, 190, 17, 88, 140, 170]
     cams = [synth.arc_camera(f, 200, 960, 540) for f in frames[:4]] + \
            [synth.arc_camera(f, 200, 480, 270) for f in frames[4:]]
-    # voxel centroids on the walls give many near-equal depths among the high-weight fragments, so
-    # a larger share of pixels carries a possible order flip (all compared pixels must match)
-    _sampled_parity(orc, g, cams, 120, 12, dev, ("mean4", "logscale4", "ql", "qr", "opacity", "rgb"), min_checked=0.6)
+    # voxel centroids on the walls give many near-equal depths among the high-weight fragments, and
+    # the 3-NN spatial scale overlaps ~15 of them per pixel, so about 45% of the sampled pixels carry
+    # a possible order flip (every compared pixel must match)
+    _sampled_parity(orc, g, cams, 120, 12, dev, ("mean4", "logscale4", "ql", "qr", "opacity", "rgb"), min_checked=0.5)

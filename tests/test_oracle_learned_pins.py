@@ -100,3 +100,20 @@ def test_knn_features_match_kdtree():
         assert knn3[i] == pytest.approx(d[i, 1:4].mean(), rel=1e-12)
     assert np.allclose(feats[:, 49:52], rgb) and np.allclose(feats[:, 52], t)
     assert np.allclose(feats[:, 48], np.linalg.norm(xyz.astype(np.float64) - [0.5, 0.5, -2.0], axis=1))
+
+
+def test_knn3_scale_matches_brute_force_window_search():
+    """The k-d tree 3-NN scale equals the brute-force window search, including sparse points with
+    fewer than 3 neighbours in the window, neighbours cut off by the window and duplicate points."""
+    pytest.importorskip("scipy.spatial")
+    r = np.random.default_rng(8)
+    voxel = 0.05
+    dense = r.uniform(0, 0.3, size=(600, 3))
+    sparse = r.uniform(1.0, 3.0, size=(60, 3))           # mostly isolated: fewer than 3 in the window
+    dup = dense[:20] + 0.0                               # exact duplicates: zero distances
+    xyz = np.concatenate([dense, sparse, dup]).astype(np.float32)
+    n = xyz.shape[0]
+    _, want, _ = OL.knn_features(xyz, np.zeros((n, 3)), np.zeros(n), np.zeros(n, np.uint8), voxel, (0, 0, 0), radius=2)
+    got = OL.knn3_scale(xyz, voxel, radius=2, k0=4)      # small first query exercises the widening
+    assert np.sum(want == voxel) >= 10                   # the fallback case is covered
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
