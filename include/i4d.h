@@ -33,7 +33,9 @@
  *   Gradients use the same flat layout.
  *   Projected records: 4 planes of V x N float4 (view-major within a plane): plane 0 (u, v,
  *   conic_a, conic_b), plane 1 (conic_c, o_t, r, g), plane 2 (b, depth, radius, 0), plane 3 the
- *   pixel-space box (xmin, xmax, ymin, ymax) of the q <= q_max ellipse, widened by 1% + 0.01 px.
+ *   blendable box: the pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_b, with
+ *   q_b = min(q_max, max(2 ln(o_t / alpha_min), 0) + 1e-3) the largest q at which alpha =
+ *   o_t exp(-q/2) can reach alpha_min, widened by 1% + 0.01 px (empty (1, 0, 1, 0) when culled).
  *   2D gradients (scratch of the backward): 3 planes of V x N float4: (du, dv, dconic_a,
  *   dconic_b), (dconic_c, do_t, dr, dg), (db, 0, 0, 0).
  *   Images: per view, planar float32 [3][H][W]; views concatenated in order.  Per-pixel
@@ -137,7 +139,10 @@ I4D_API int64_t i4d_param_floats(int32_t sh_deg);
  * i4d_slice_project -- Eq. 7-8 (conditional mean mu_xyz|t and covariance Sigma_xyz|t of each 4D
  * Gaussian at each view's frame time), the temporal marginal opacity o_t = sigmoid(o) N(t; mu_t,
  * Sigma_44) with its cull below settings.ot_min (Sec. 3.3, Eq. 9), EWA projection to 2D, colour
- * (base RGB + real SH of degree 1..3 of the view direction) and the tile rectangle.
+ * (base RGB + real SH of degree 1..3 of the view direction), the blendable box and the tile
+ * rectangle: the tiles [floor((xmin + 0.5) / tile_w), floor((xmax - 0.5) / tile_w) + 1) x (same in
+ * y) that hold a pixel centre of the box, clipped to the view.  Every pixel where the Gaussian can
+ * be blended lies in it, so the image equals that of the 3-sigma square of 3D splatting.
  *   g        host struct, params on the device
  *   views    host; cams: DEVICE array of views->n_views cameras
  *   settings host (NULL = defaults)

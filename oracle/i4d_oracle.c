@@ -324,17 +324,36 @@ static void forward_one(int i, int sh_deg, int mode, const double* mean4, const 
     }
   }
 
-  /* tile rectangle [x0,x1) x [y0,y1) of the tiles the radius-r square touches */
+  /*
+   * Tile rectangle.  A fragment is blended only where q <= q_max and alpha = o_t exp(-q/2) >=
+   * alpha_min, i.e. inside the ellipse q <= q_b = min(q_max, max(2 ln(o_t / alpha_min), 0) + 1e-3)
+   * (the 1e-3 keeps the bound conservative under rounding).  The blendable box holds that ellipse:
+   * half-widths sqrt(q_b Sigma2_xx) and sqrt(q_b Sigma2_yy) (the inverse conic's diagonal), widened
+   * by 1% + 0.01 px.  The rectangle [x0,x1) x [y0,y1) is the set of tiles holding a pixel centre
+   * p + 0.5 of the box, clipped to the view; an empty rectangle culls the Gaussian in this view.
+   * Outside the box no pixel can be blended, so the image is the one a 3-sigma square would give.
+   */
   if (vis) {
     const int tx = (int)((cam[C_W] + tile_w - 1) / tile_w), ty = (int)((cam[C_H] + tile_h - 1) / tile_h);
-    const double ax0 = (f->u - f->radius) / tile_w, ax1 = (f->u + f->radius) / tile_w;
-    const double ay0 = (f->v - f->radius) / tile_h, ay1 = (f->v + f->radius) / tile_h;
+    const double qa = 2.0 * log(f->ot / S[S_ALPHA_MIN]);
+    const double qb = fmin(S[S_Q_MAX], (qa > 0.0 ? qa : 0.0) + 1e-3);
+    const double cdet = f->conic[0] * f->conic[2] - f->conic[1] * f->conic[1];
+    const double hx = sqrt(qb * f->conic[2] / cdet) * 1.01 + 0.01;
+    const double hy = sqrt(qb * f->conic[0] / cdet) * 1.01 + 0.01;
+    const double ax0 = (f->u - hx + 0.5) / tile_w, ax1 = (f->u + hx - 0.5) / tile_w;
+    const double ay0 = (f->v - hy + 0.5) / tile_h, ay1 = (f->v + hy - 0.5) / tile_h;
     double x0 = floor(ax0), x1 = floor(ax1) + 1.0, y0 = floor(ay0), y1 = floor(ay1) + 1.0;
     x0 = fmin(fmax(x0, 0.0), tx); x1 = fmin(fmax(x1, 0.0), tx);
     y0 = fmin(fmax(y0, 0.0), ty); y1 = fmin(fmax(y1, 0.0), ty);
+    if (x1 < x0) x1 = x0;
+    if (y1 < y0) y1 = y0;
     f->rect[0] = (int)x0; f->rect[1] = (int)y0; f->rect[2] = (int)x1; f->rect[3] = (int)y1;
+    /* closeness of an edge to a tile boundary, relative to the edge's coordinate and to the FP32
+       uncertainty of the half-widths, which grows with the ellipse's condition number */
+    const double cond = f->lam * f->lam / f->det;
+    const double unc = (fmax(hx, hy) / fmin(tile_w, tile_h)) * cond * 1e-3;
     double rm = fmin(fmin(frac_margin(ax0), frac_margin(ax1)), fmin(frac_margin(ay0), frac_margin(ay1)));
-    f->rect_margin = fmin(f->rect_margin, rm / fmax(fabs(ax1), 1.0));
+    f->rect_margin = fmin(f->rect_margin, rm / (fmax(fmax(fabs(ax1), fabs(ay1)), 1.0) + unc));
     if ((f->rect[2] - f->rect[0]) * (f->rect[3] - f->rect[1]) == 0) vis = 0;
   }
   f->visible = vis;

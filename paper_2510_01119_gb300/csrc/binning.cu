@@ -156,10 +156,8 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, c
   const uint32_t r = rec[k];
   const int v = (int)(r / (uint32_t)n);
   const uint32_t id = r - (uint32_t)v * (uint32_t)n;
-  const float4 a = proj[r];
-  const float4 c = proj[2 * VN + r];
   int x0, y0, x1, y1;
-  tile_rect(a.x, a.y, c.z, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+  box_rect(proj[3 * VN + r], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
   int64_t o = offs[k];
   const uint32_t base = (uint32_t)vt.tile_off[v];
   for (int ty = y0; ty < y1; ++ty)

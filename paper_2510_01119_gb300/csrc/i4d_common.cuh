@@ -50,16 +50,28 @@ I4D_D int view_of_tile(const ViewTable& vt, int tile) {
 
 // Tile rectangle [x0, x1) x [y0, y1) of the square of half-width `radius` around (u, v).
 // The same function is used when counting and when emitting, so both agree bit for bit.
-I4D_D void tile_rect(float u, float v, float radius, int tile_w, int tile_h, int tiles_x, int tiles_y,
-                     int& x0, int& y0, int& x1, int& y1) {
-  const float fx0 = floorf((u - radius) / (float)tile_w);
-  const float fx1 = floorf((u + radius) / (float)tile_w) + 1.0f;
-  const float fy0 = floorf((v - radius) / (float)tile_h);
-  const float fy1 = floorf((v + radius) / (float)tile_h) + 1.0f;
+I4D_D void box_rect(float4 b, int tile_w, int tile_h, int tiles_x, int tiles_y, int& x0, int& y0, int& x1,
+                    int& y1) {
+  // tiles [x0,x1) x [y0,y1) holding the pixels whose centres (p + 0.5) lie in the box
+  const float fx0 = floorf((b.x + 0.5f) / (float)tile_w);
+  const float fx1 = floorf((b.y - 0.5f) / (float)tile_w) + 1.0f;
+  const float fy0 = floorf((b.z + 0.5f) / (float)tile_h);
+  const float fy1 = floorf((b.w - 0.5f) / (float)tile_h) + 1.0f;
   x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)tiles_x);
   x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)tiles_x);
   y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)tiles_y);
   y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)tiles_y);
+  x1 = max(x1, x0);
+  y1 = max(y1, y0);
+}
+
+// Largest q at which a fragment of temporal opacity ot can be blended: coverage ends at q_max, and
+// alpha = ot exp(-q/2) reaches alpha_min only while q <= 2 ln(ot / alpha_min).  The 1e-3 slack
+// covers the rounding of the fast exponential and of the product in eval_fragment (relative errors
+// of a few 1e-7), so every fragment that eval_fragment keeps lies inside the resulting ellipse.
+I4D_D float blend_q(float ot, const Settings& s) {
+  const float qa = 2.0f * logf(ot / s.alpha_min);
+  return fminf(s.q_max, fmaxf(qa, 0.0f) + 1e-3f);
 }
 
 // Fragment evaluation shared by the forward and the backward compositing kernels: q, the
@@ -80,9 +92,11 @@ I4D_D bool eval_fragment(float dx, float dy, float ca, float cb, float cc, float
 
 // Pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max of a conic, widened by
 // 1% + 0.01 px so that float rounding can never exclude a pixel centre that the per-pixel test
-// accepts (the half-widths are 3 sqrt of the diagonal of the inverse conic).
+// accepts (the half-widths are sqrt(q_max) times the square roots of the inverse conic's diagonal).
 I4D_D float4 ellipse_box(float u, float v, float ca, float cb, float cc, float q_max) {
-  const float det = ca * cc - cb * cb;
+  // ca cc - cb^2 by Kahan's difference of products: accurate to a few ulp however thin the ellipse
+  const float w = __fmul_rn(cb, cb);
+  const float det = __fadd_rn(__fmaf_rn(ca, cc, -w), __fmaf_rn(-cb, cb, w));
   if (!(det > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
   const float hx = sqrtf(q_max * cc / det) * 1.01f + 0.01f;
   const float hy = sqrtf(q_max * ca / det) * 1.01f + 0.01f;

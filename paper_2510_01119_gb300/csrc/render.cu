@@ -7,7 +7,7 @@
 // the blocks of its two halves, and stages the hits of each half -- compacted in list order by a
 // ballot and a prefix count -- in that half's shared-memory slots; each half's pixels then visit
 // only those hits, the two halves side by side.  The test is exact: the box holds every pixel
-// centre with q <= q_max.  A warp stops as soon as all its pixels are saturated (forward) or when
+// centre where the fragment can be blended (q <= q_max and alpha >= alpha_min).  A warp stops as soon as all its pixels are saturated (forward) or when
 // it has passed its pixels' last blended fragments (backward).
 // The backward walks the list back to front, recovering the transmittance from T_final by division
 // (no per-fragment state), and sums each Gaussian's nine 2D-gradient components over its half-warp

@@ -1,8 +1,9 @@
-// Slice + project (Eq. 7-9, EWA, SH colour, tile rectangle) and its backward chain.
+// Slice + project (Eq. 7-9, EWA, SH colour, blendable extent and tile rectangle) and its backward
+// chain.
 //
 // One thread per Gaussian loops over all views of the batch: the view-independent part (rotation,
 // 4D covariance, sigmoid) is computed once and the parameters are read from HBM once per launch,
-// not once per view.  Records are written as three float4 planes so every store is coalesced.
+// not once per view.  Records are written as four float4 planes so every store is coalesced.
 #include "gauss_math.cuh"
 #include "kernels.cuh"
 
@@ -50,17 +51,19 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
     ViewFwd F;
     view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F);
     uint32_t cnt = 0;
+    float4 box = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // empty
     if (F.visible) {
+      // screen extent where a fragment can be blended (q <= q_max and alpha >= alpha_min)
+      box = ellipse_box(F.u, F.v, F.conic[0], F.conic[1], F.conic[2], blend_q(F.ot, S));
       int x0, y0, x1, y1;
-      tile_rect(F.u, F.v, F.radius, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+      box_rect(box, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
       cnt = (uint32_t)((x1 - x0) * (y1 - y0));
     }
     const size_t r = (size_t)v * n + i;
     proj[r] = make_float4(F.u, F.v, F.conic[0], F.conic[1]);
     proj[VN + r] = make_float4(F.conic[2], F.ot, fmaxf(F.raw[0], 0.0f), fmaxf(F.raw[1], 0.0f));
     proj[2 * VN + r] = make_float4(fmaxf(F.raw[2], 0.0f), F.m[2], F.radius, 0.0f);
-    proj[3 * VN + r] = F.visible ? ellipse_box(F.u, F.v, F.conic[0], F.conic[1], F.conic[2], S.q_max)
-                                 : make_float4(1.0f, 0.0f, 1.0f, 0.0f);
+    proj[3 * VN + r] = box;
     touched[r] = cnt;
   }
 }

@@ -377,7 +377,19 @@ def test_backward_matches_central_differences(orc, mode, cutoffs):
 # ---------------------------------------------------------------------------------------------
 # tile pairs
 # ---------------------------------------------------------------------------------------------
-def test_tile_pairs_cover_every_covered_pixel_in_order(orc):
+def _blendable_tiles(P, i, C, W, H, tile=16):
+    """Brute force: the tiles holding a pixel where Gaussian i can be blended (q <= 9 and
+    o_t exp(-q/2) >= 1/255), and the tiles holding a pixel with q <= 9 (the 3-sigma ellipse)."""
+    ys, xs = np.divmod(np.arange(W * H), W)
+    dx, dy = xs + 0.5 - P[i, C["u"]], ys + 0.5 - P[i, C["v"]]
+    q = P[i, C["ca"]] * dx * dx + 2 * P[i, C["cb"]] * dx * dy + P[i, C["cc"]] * dy * dy
+    tx = (W + tile - 1) // tile
+    t_of = (ys // tile) * tx + xs // tile
+    blend = (q <= 9) & (P[i, C["ot"]] * np.exp(-0.5 * q) >= 1 / 255)
+    return set(t_of[blend].tolist()), set(t_of[q <= 9].tolist())
+
+
+def test_tile_pairs_cover_every_blendable_pixel_in_order(orc):
     g = synth.gaussians_uniform(0)
     cam = synth.camera(128, 96, time=0.5)
     P = orc.project(g, cam)
@@ -386,13 +398,52 @@ def test_tile_pairs_cover_every_covered_pixel_in_order(orc):
     # order: tile ascending, then depth, then id
     key = list(zip(tiles, P[ids, C["depth"]], ids))
     assert key == sorted(key)
-    have = set(zip(tiles.tolist(), ids.tolist()))
-    ys, xs = np.divmod(np.arange(128 * 96), 128)
-    for i in np.where(P[:, C["visible"]] != 0)[0]:
-        dx, dy = xs + 0.5 - P[i, C["u"]], ys + 0.5 - P[i, C["v"]]
-        q = P[i, C["ca"]] * dx * dx + 2 * P[i, C["cb"]] * dx * dy + P[i, C["cc"]] * dy * dy
-        for p in np.where(q <= 9)[0]:
-            assert ((ys[p] // 16) * 8 + xs[p] // 16, i) in have
+    have = {}
+    for t, i in zip(tiles.tolist(), ids.tolist()):
+        have.setdefault(i, set()).add(t)
+    need_total = sigma3_total = 0
+    for i in range(P.shape[0]):
+        need, sigma3 = _blendable_tiles(P, i, C, 128, 96)
+        assert need <= have.get(i, set()), i        # no blendable pixel is lost
+        if not need:
+            continue
+        need_total += len(need)
+        sigma3_total += len(sigma3)
+    # the rectangle is the box of an ellipse: a little larger than the tiles it needs, and smaller
+    # than the 3-sigma extent because low-opacity fragments fade below 1/255 before q = 9
+    assert need_total <= len(tiles) <= 1.5 * need_total
+    assert len(tiles) < sigma3_total
+
+
+def test_tile_rectangle_shrinks_with_temporal_opacity(orc):
+    """One isotropic Gaussian facing the camera, 4x4 tiles: the rectangle spans the tiles of the
+    pixels where the Gaussian can be blended, to within one tile per side.  At o_t = 0.2 those end
+    at q = 2 ln(51) < 9, inside the 3-sigma ellipse; just above the cull (o_t = 1.02/255) they end
+    at 0.2 sigma; at o_t = 0.99 the 3-sigma ellipse binds."""
+    W = 1024
+    cam = synth.camera(W, W, 60.0, time=0.5)
+    C = orc.P
+    ys, xs = np.divmod(np.arange(W * W), W)
+    spans = {}
+    for ot in (0.2, 1.02 / 255, 0.99):
+        logit = math.log(ot / (1 - ot))
+        g = dict(mean4=np.array([[0.0, 0.0, 3.0, 0.5]]), logscale4=np.log([[0.3, 0.3, 0.3, 1e3]]),
+                 ql=np.array([[1.0, 0, 0, 0]]), qr=np.array([[1.0, 0, 0, 0]]), opacity=np.array([logit]),
+                 rgb=np.ones((1, 3)), sh=np.zeros((1, 0, 3)), sh_deg=0, mode=0)
+        P = orc.project(g, cam, tile=(4, 4))
+        assert P[0, C["ot"]] == pytest.approx(ot, rel=1e-6)
+        dx, dy = xs + 0.5 - P[0, C["u"]], ys + 0.5 - P[0, C["v"]]
+        q = P[0, C["ca"]] * dx * dx + 2 * P[0, C["cb"]] * dx * dy + P[0, C["cc"]] * dy * dy
+        blend = (q <= 9) & (ot * np.exp(-0.5 * q) >= 1 / 255)
+        bx, by = xs[blend] // 4, ys[blend] // 4
+        x0, x1, y0, y1 = (int(P[0, C[k]]) for k in ("x0", "x1", "y0", "y1"))
+        assert x0 <= bx.min() and bx.max() < x1 and y0 <= by.min() and by.max() < y1
+        assert x0 >= bx.min() - 1 and x1 <= bx.max() + 2 and y0 >= by.min() - 1 and y1 <= by.max() + 2
+        s3 = xs[q <= 9] // 4
+        spans[ot] = (x1 - x0, s3.max() - s3.min() + 1)
+    assert spans[0.2][0] < spans[0.2][1] - 2           # narrower than the 3-sigma extent
+    assert spans[1.02 / 255][0] < spans[0.2][0] / 5      # sigma sqrt(2 ln 1.02) = 0.2 sigma
+    assert spans[0.99][0] >= spans[0.99][1]
 
 
 # ---------------------------------------------------------------------------------------------
