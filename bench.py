@@ -242,6 +242,20 @@ def algorithmic_bytes(kernel: str, n: int, V: int, I: int, R_vis: int, P: int, p
     return float("nan")
 
 
+# FP32 operations (an FMA counts 2) the compositing must spend on each blended (pixel, Gaussian)
+# pair, not counting the fast exponential / reciprocal: forward = q from the conic (8), the q and
+# alpha tests, exp argument and alpha (8.5), transmittance update and colour (10); backward = the
+# same evaluation (16.5), transmittance recovery (3), colour and alpha gradients (26), gradients
+# of the mean and conic (26).
+FLOPS_PER_BLENDED_PAIR = {"render_fwd": 26.0, "render_bwd": 72.0}
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 FLOP x clock (the median SM clock under load)."""
+    return sms * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
+
+
 # kernels per profiled scope (memsets are not kernels; one scan scope launches three kernels)
 KERNELS_PER_SCOPE = {"scan": 3, "grad2d_clear": 0, "adam": 2, "loss": 1}
 
@@ -476,6 +490,7 @@ def run_ours(args, ws, rank, local):
     I = int(step.rast.n_inst.item())
     R_vis = int((step.rast.touched[:V * n] > 0).sum().item())
     P = step.rast.total_pixels
+    E = int(step.rast.n_contrib[:P].to(torch.int64).sum().item())  # blended pairs of the last step
     bits = 32 + int(np.ceil(np.log2(max(step.rast.total_tiles, 2))))
     passes = (bits + 7) // 8
     per_step = {k: v[0] / args.profile_steps for k, v in prof.items()}
@@ -489,6 +504,22 @@ def run_ours(args, ws, rank, local):
     hbm_peak, peak_kind = measured_peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
     traffic = stored_traffic(dominant)
+    hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+           "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic, "algorithmic_bytes": alg}
+    if dominant in FLOPS_PER_BLENDED_PAIR:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_mhz") or 2070.0
+        peak = fp32_peak_tflops(sms, mhz)
+        flops = E * FLOPS_PER_BLENDED_PAIR[dominant]
+        ach = flops / (dom_ms * 1e-3) / 1e12
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": traffic, "ms_per_launch": dom_ms,
+                    "peak_kind": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz (median "
+                                 f"SM clock under load)",
+                    "algorithmic_flops": flops, "blended_pairs": E,
+                    "flops_per_pair": FLOPS_PER_BLENDED_PAIR[dominant], "hbm": hbm}
+    else:
+        roofline = {"kernel": dominant, "bound": "hbm", "ms_per_launch": dom_ms, **hbm}
 
     value = ws * 1000.0 / ms_max
     line = {
@@ -505,9 +536,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * 1000.0 / e2e_ms, "unit": "it/s",
                 "h2d_bytes_per_step": int(step.target.numel() * 4 + V * 80), "d2h_bytes_per_step": 4},
         "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "traffic": traffic, "algorithmic_bytes": alg, "ms_per_launch": dom_ms},
+        "roofline": roofline,
         "kernels_ms_per_step": {k: round(v, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
         "kernel_share": {k: round(v / tot, 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1])},
         "prune": {"ms": wl["prune_ms"], "points": wl["points"],

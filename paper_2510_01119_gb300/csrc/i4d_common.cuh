@@ -67,27 +67,37 @@ I4D_D void box_rect(float4 b, int tile_w, int tile_h, int tiles_x, int tiles_y, 
 
 // Largest q at which a fragment of temporal opacity ot can be blended: coverage ends at q_max, and
 // alpha = ot exp(-q/2) reaches alpha_min only while q <= 2 ln(ot / alpha_min).  The 1e-3 slack
-// covers the rounding of the fast exponential and of the product in eval_fragment (relative errors
-// of a few 1e-7), so every fragment that eval_fragment keeps lies inside the resulting ellipse.
+// covers the rounding of the fast exponential and of the product in eval_pair (relative errors of a
+// few 1e-7), so every fragment that eval_pair keeps lies inside the resulting ellipse.
 I4D_D float blend_q(float ot, const Settings& s) {
   const float qa = 2.0f * logf(ot / s.alpha_min);
   return fminf(s.q_max, fmaxf(qa, 0.0f) + 1e-3f);
 }
 
-// Fragment evaluation shared by the forward and the backward compositing kernels: q, the
-// Gaussian falloff G = exp(-q/2) and the raw alpha o_t G.  Returns false when the fragment is
-// skipped (outside the q_max ellipse or alpha below alpha_min).  Both kernels call exactly this
+// One Gaussian evaluated at a thread's two pixels (same column, offsets dx and dy.x / dy.y from the
+// projected mean): q = ca dx^2 + 2 cb dx dy + cc dy^2, the falloff G = exp(-q/2), the raw alpha
+// o_t G and the clamped alpha; kept = inside the q_max ellipse and alpha >= alpha_min.  The pixel
+// pair runs on the packed FP32x2 instructions of sm_100 and later (__fmul2_rn / __ffma2_rn round
+// each lane exactly as __fmul_rn / __fmaf_rn), so every value equals the scalar computation with
+// these explicit roundings.  The forward and the backward compositing kernels call exactly this
 // code on the same inputs, so they take the same decisions.
-I4D_D bool eval_fragment(float dx, float dy, float ca, float cb, float cc, float ot, const Settings& s, float& q,
-                         float& G, float& a_raw, float& alpha) {
-  // explicit roundings: no compiler contraction can make the two kernels differ
-  q = __fmaf_rn(cc, __fmul_rn(dy, dy),
-                __fmaf_rn(__fmul_rn(2.0f, cb), __fmul_rn(dx, dy), __fmul_rn(ca, __fmul_rn(dx, dx))));
-  if (!(q <= s.q_max)) return false;
-  G = __expf(__fmul_rn(-0.5f, q));
-  a_raw = __fmul_rn(ot, G);
-  alpha = fminf(s.alpha_max, a_raw);
-  return alpha >= s.alpha_min;
+struct FragPair {
+  float2 q, G, a_raw, alpha, dxdy, dydy;
+  bool k0, k1;
+};
+
+I4D_D void eval_pair(float dx, float2 dy, float ca, float cb, float cc, float ot, const Settings& s, FragPair& f) {
+  const float t0 = __fmul_rn(ca, __fmul_rn(dx, dx));
+  const float c2b = __fmul_rn(2.0f, cb);
+  f.dxdy = __fmul2_rn(make_float2(dx, dx), dy);
+  f.dydy = __fmul2_rn(dy, dy);
+  f.q = __ffma2_rn(make_float2(cc, cc), f.dydy, __ffma2_rn(make_float2(c2b, c2b), f.dxdy, make_float2(t0, t0)));
+  const float2 m = __fmul2_rn(make_float2(-0.5f, -0.5f), f.q);
+  f.G = make_float2(__expf(m.x), __expf(m.y));
+  f.a_raw = __fmul2_rn(make_float2(ot, ot), f.G);
+  f.alpha = make_float2(fminf(s.alpha_max, f.a_raw.x), fminf(s.alpha_max, f.a_raw.y));
+  f.k0 = f.q.x <= s.q_max && f.alpha.x >= s.alpha_min;
+  f.k1 = f.q.y <= s.q_max && f.alpha.y >= s.alpha_min;
 }
 
 // Pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max of a conic, widened by

@@ -1,7 +1,8 @@
 // Front-to-back compositing of all views' tiles in one launch, and its backward.
 //
 // One CTA per (view, tile), taken longest list first.  Each 16-lane half-warp owns an 8x4 pixel
-// block of the tile and each thread two vertically adjacent pixels.  The warps of a CTA never
+// block of the tile and each thread two vertically adjacent pixels, whose arithmetic runs side by
+// side on the packed FP32x2 instructions (one instruction per operation for both pixels).  The warps of a CTA never
 // synchronise with one another: each warp streams its tile's depth-sorted list in chunks of 32
 // entries, one entry per lane, tests the entry's ellipse box (precomputed by slice_project) against
 // the blocks of its two halves, and stages the hits of each half -- compacted in list order by a
@@ -125,9 +126,11 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
   const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
   const size_t VN = (size_t)vt.n_views * n;
   const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
-  const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
-  float T0 = 1.0f, T1 = 1.0f;
-  float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+  const float fx = (float)wp.px + 0.5f;
+  const float2 fy = make_float2((float)wp.py0 + 0.5f, (float)wp.py0 + 1.5f);
+  // the thread's two pixels side by side in float2 lanes: transmittance and colour
+  float2 T = make_float2(1.0f, 1.0f);
+  float2 Cr = make_float2(0.0f, 0.0f), Cg = Cr, Cb = Cr;
   uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
   bool done0 = !in0, done1 = !in1;
   for (uint32_t base = rs; base < re; base += 32) {
@@ -138,35 +141,27 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
       const float4 a = mine.a[t];
       const float4 b = mine.b[t];
       const float dx = __fsub_rn(fx, a.x);
-      float q, G, ar, al;
-      if (!done0 && eval_fragment(dx, __fsub_rn(fy0, a.y), a.z, a.w, b.x, b.y, S, q, G, ar, al)) {
-        const float Tn = __fmul_rn(T0, __fsub_rn(1.0f, al));
-        if (Tn < S.T_min) {
-          done0 = true;
-        } else {
-          const float w = al * T0;
-          C00 += w * b.z;
-          C01 += w * b.w;
-          C02 += w * mine.c2[t];
-          T0 = Tn;
-          last0 = mine.pos[t] + 1u;
-          ++cnt0;
-        }
-      }
-      if (!done1 && eval_fragment(dx, __fsub_rn(fy1, a.y), a.z, a.w, b.x, b.y, S, q, G, ar, al)) {
-        const float Tn = __fmul_rn(T1, __fsub_rn(1.0f, al));
-        if (Tn < S.T_min) {
-          done1 = true;
-        } else {
-          const float w = al * T1;
-          C10 += w * b.z;
-          C11 += w * b.w;
-          C12 += w * mine.c2[t];
-          T1 = Tn;
-          last1 = mine.pos[t] + 1u;
-          ++cnt1;
-        }
-      }
+      FragPair f;
+      eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, S, f);
+      const bool k0 = f.k0 && !done0, k1 = f.k1 && !done1;
+      // a kept fragment that would take T below T_min stops the pixel without being blended
+      const float2 Tn = __fmul2_rn(T, __ffma2_rn(f.alpha, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f)));
+      const bool s0 = k0 && Tn.x < S.T_min, s1 = k1 && Tn.y < S.T_min;
+      done0 = done0 || s0;
+      done1 = done1 || s1;
+      const bool b0 = k0 && !s0, b1 = k1 && !s1;
+      // a pixel that does not blend gets weight 0, which leaves its colour unchanged exactly
+      const float2 w = __fmul2_rn(make_float2(b0 ? f.alpha.x : 0.0f, b1 ? f.alpha.y : 0.0f), T);
+      const float c2 = mine.c2[t];
+      Cr = __ffma2_rn(w, make_float2(b.z, b.z), Cr);
+      Cg = __ffma2_rn(w, make_float2(b.w, b.w), Cg);
+      Cb = __ffma2_rn(w, make_float2(c2, c2), Cb);
+      T = make_float2(b0 ? Tn.x : T.x, b1 ? Tn.y : T.y);
+      const uint32_t p1 = mine.pos[t] + 1u;
+      last0 = b0 ? p1 : last0;
+      last1 = b1 ? p1 : last1;
+      cnt0 += b0 ? 1u : 0u;
+      cnt1 += b1 ? 1u : 0u;
     }
     __syncwarp();
   }
@@ -174,59 +169,76 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
   if (in0) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
-    img[pimg] = C00 + T0 * S.bg[0];
-    img[pimg + HW] = C01 + T0 * S.bg[1];
-    img[pimg + 2 * HW] = C02 + T0 * S.bg[2];
-    T_final[p] = T0;
+    img[pimg] = Cr.x + T.x * S.bg[0];
+    img[pimg + HW] = Cg.x + T.x * S.bg[1];
+    img[pimg + 2 * HW] = Cb.x + T.x * S.bg[2];
+    T_final[p] = T.x;
     last_out[p] = last0;
     ncon[p] = cnt0;
   }
   if (in1) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
-    img[pimg] = C10 + T1 * S.bg[0];
-    img[pimg + HW] = C11 + T1 * S.bg[1];
-    img[pimg + 2 * HW] = C12 + T1 * S.bg[2];
-    T_final[p] = T1;
+    img[pimg] = Cr.y + T.y * S.bg[0];
+    img[pimg + HW] = Cg.y + T.y * S.bg[1];
+    img[pimg + 2 * HW] = Cb.y + T.y * S.bg[2];
+    T_final[p] = T.y;
     last_out[p] = last1;
     ncon[p] = cnt1;
   }
 }
 
-// Backward state of one pixel: transmittance in front of the next (nearer) fragment, colour
-// composited behind it, upstream gradient and the position of its last blended fragment.
-struct PixBwd {
-  float T, S0, S1, S2, g0, g1, g2;
-  uint32_t L;
+// Backward state of the thread's two pixels (float2 lanes): transmittance in front of the next
+// (nearer) fragment, colour composited behind it, upstream gradient, and the positions of the
+// pixels' last blended fragments.
+struct PairBwd {
+  float2 T, Sr, Sg, Sb, ur, ug, ub;
+  uint32_t L0, L1;
 };
 
-// Gradient contribution of one fragment at one pixel (accumulated into g[9]).
-__device__ __forceinline__ bool pixel_grad(PixBwd& P, float dx, float dy, const float4& a, const float4& b, float c2,
-                                           const Settings& S, float* g) {
-  float q, G, ar, al;
-  if (!eval_fragment(dx, dy, a.z, a.w, b.x, b.y, S, q, G, ar, al)) return false;
-  const float om = 1.0f - al;
-  const float iom = __fdividef(1.0f, om);
-  const float Tk = P.T * iom;  // transmittance in front of this fragment
-  const float w = al * Tk;
-  g[6] += w * P.g0;
-  g[7] += w * P.g1;
-  g[8] += w * P.g2;
-  const float dA = P.g0 * (Tk * b.z - P.S0 * iom) + P.g1 * (Tk * b.w - P.S1 * iom) + P.g2 * (Tk * c2 - P.S2 * iom);
-  P.S0 += w * b.z;
-  P.S1 += w * b.w;
-  P.S2 += w * c2;
-  P.T = Tk;
-  if (ar < S.alpha_max) {
-    g[5] += dA * G;
-    const float dq = -0.5f * ar * dA;
-    g[0] += -2.0f * dq * (a.z * dx + a.w * dy);
-    g[1] += -2.0f * dq * (a.w * dx + b.x * dy);
-    g[2] += dq * dx * dx;
-    g[3] += 2.0f * dq * dx * dy;
-    g[4] += dq * dy * dy;
-  }
-  return true;
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// Gradient of one fragment at the thread's two pixels, summed over the pixels into g[9] (the 2D
+// record components du, dv, dconic_a, dconic_b, dconic_c, do_t, dr, dg, db).  k0 / k1 say which
+// pixel blended this fragment in the forward; the other lane gets weight 0 and stays unchanged.
+__device__ __forceinline__ void pair_grad(PairBwd& P, float dx, float2 dy, const FragPair& f, bool k0, bool k1,
+                                          const float4& a, const float4& b, float c2, const Settings& S, float* g) {
+  const float2 om = __ffma2_rn(f.alpha, f2(-1.0f), f2(1.0f));
+  const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+  const float2 niom = __fmul2_rn(iom, f2(-1.0f));
+  const float2 Tk = __fmul2_rn(P.T, iom);  // transmittance in front of this fragment
+  const float2 w = __fmul2_rn(make_float2(k0 ? f.alpha.x : 0.0f, k1 ? f.alpha.y : 0.0f), Tk);
+  // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)), S_c the colour composited behind
+  const float2 xr = __ffma2_rn(Tk, f2(b.z), __fmul2_rn(P.Sr, niom));
+  const float2 xg = __ffma2_rn(Tk, f2(b.w), __fmul2_rn(P.Sg, niom));
+  const float2 xb = __ffma2_rn(Tk, f2(c2), __fmul2_rn(P.Sb, niom));
+  const float2 dA = __ffma2_rn(P.ub, xb, __ffma2_rn(P.ug, xg, __fmul2_rn(P.ur, xr)));
+  const float2 s6 = __fmul2_rn(w, P.ur), s7 = __fmul2_rn(w, P.ug), s8 = __fmul2_rn(w, P.ub);
+  P.Sr = __ffma2_rn(w, f2(b.z), P.Sr);
+  P.Sg = __ffma2_rn(w, f2(b.w), P.Sg);
+  P.Sb = __ffma2_rn(w, f2(c2), P.Sb);
+  P.T = make_float2(k0 ? Tk.x : P.T.x, k1 ? Tk.y : P.T.y);
+  // through alpha = o_t G (zero where the 0.99 cap binds): do_t = dA G, and with
+  // dq = -dA o_t G / 2 = -p / 2: du = p (ca dx + cb dy), dv = p (cb dx + cc dy),
+  // dconic = (dq dx^2, 2 dq dx dy, dq dy^2)
+  const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
+  const float2 dAe = make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f);
+  const float2 s5 = __fmul2_rn(dAe, f.G);
+  const float2 p = __fmul2_rn(f.a_raw, dAe);
+  const float2 s0 = __fmul2_rn(p, __ffma2_rn(f2(a.w), dy, f2(__fmul_rn(a.z, dx))));
+  const float2 s1 = __fmul2_rn(p, __ffma2_rn(f2(b.x), dy, f2(__fmul_rn(a.w, dx))));
+  const float2 s2 = __fmul2_rn(p, f2(__fmul_rn(-0.5f, __fmul_rn(dx, dx))));
+  const float2 s3 = __fmul2_rn(__fmul2_rn(p, f2(-1.0f)), f.dxdy);
+  const float2 s4 = __fmul2_rn(p, __fmul2_rn(f2(-0.5f), f.dydy));
+  g[0] = s0.x + s0.y;
+  g[1] = s1.x + s1.y;
+  g[2] = s2.x + s2.y;
+  g[3] = s3.x + s3.y;
+  g[4] = s4.x + s4.y;
+  g[5] = s5.x + s5.y;
+  g[6] = s6.x + s6.y;
+  g[7] = s7.x + s7.y;
+  g[8] = s8.x + s8.y;
 }
 
 // Sum g[0..7] over each 16-lane half so that lane l of a half ends up with the half's total of
@@ -281,35 +293,35 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
   const size_t VN = (size_t)vt.n_views * n;
   const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
-  const float fx = (float)wp.px + 0.5f, fy0 = (float)wp.py0 + 0.5f, fy1 = fy0 + 1.0f;
+  const float fx = (float)wp.px + 0.5f;
+  const float2 fy = make_float2((float)wp.py0 + 0.5f, (float)wp.py0 + 1.5f);
   const int64_t HW = (int64_t)tc.W * tc.H;
-  PixBwd P0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, P1{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+  PairBwd P;
+  P.T = P.Sr = P.Sg = P.Sb = P.ur = P.ug = P.ub = f2(0.0f);
+  P.L0 = P.L1 = 0u;
   if (in0) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
-    P0.T = T_final[p];
-    P0.L = last_in[p];
-    P0.g0 = dimg[pimg];
-    P0.g1 = dimg[pimg + HW];
-    P0.g2 = dimg[pimg + 2 * HW];
-    P0.S0 = P0.T * S.bg[0];
-    P0.S1 = P0.T * S.bg[1];
-    P0.S2 = P0.T * S.bg[2];
+    P.T.x = T_final[p];
+    P.L0 = last_in[p];
+    P.ur.x = dimg[pimg];
+    P.ug.x = dimg[pimg + HW];
+    P.ub.x = dimg[pimg + 2 * HW];
   }
   if (in1) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
-    P1.T = T_final[p];
-    P1.L = last_in[p];
-    P1.g0 = dimg[pimg];
-    P1.g1 = dimg[pimg + HW];
-    P1.g2 = dimg[pimg + 2 * HW];
-    P1.S0 = P1.T * S.bg[0];
-    P1.S1 = P1.T * S.bg[1];
-    P1.S2 = P1.T * S.bg[2];
+    P.T.y = T_final[p];
+    P.L1 = last_in[p];
+    P.ur.y = dimg[pimg];
+    P.ug.y = dimg[pimg + HW];
+    P.ub.y = dimg[pimg + 2 * HW];
   }
+  P.Sr = __fmul2_rn(P.T, f2(S.bg[0]));
+  P.Sg = __fmul2_rn(P.T, f2(S.bg[1]));
+  P.Sb = __fmul2_rn(P.T, f2(S.bg[2]));
   // this warp never needs entries past its pixels' last blended fragments
-  const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P0.L, P1.L));
+  const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P.L0, P.L1));
   const uint32_t end = rs + min(wL, re - rs);
   // component c of a 2D-gradient record lives in plane c / 4, lane c % 4 (c = 8: plane 2, lane 0)
   const int comp = (lane >> 1) & 7;
@@ -332,8 +344,13 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
         const uint32_t pos = mine.pos[t];
         rr = mine.rec[t];
         const float dx = __fsub_rn(fx, a.x);
-        if (in0 && pos < P0.L) any |= pixel_grad(P0, dx, __fsub_rn(fy0, a.y), a, b, c2, S, g);
-        if (in1 && pos < P1.L) any |= pixel_grad(P1, dx, __fsub_rn(fy1, a.y), a, b, c2, S, g);
+        const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
+        FragPair f;
+        eval_pair(dx, dy, a.z, a.w, b.x, b.y, S, f);
+        // the fragments a pixel blended are the kept ones before its last (out-of-view pixels: L = 0)
+        const bool k0 = f.k0 && pos < P.L0, k1 = f.k1 && pos < P.L1;
+        any = k0 || k1;
+        if (any) pair_grad(P, dx, dy, f, k0, k1, a, b, c2, S, g);
       }
       const unsigned vm = __ballot_sync(0xffffffffu, any);
       if (vm) {
