@@ -173,9 +173,17 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, c
 // ---- radix sort ---------------------------------------------------------------------------------------
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;                          // keys per thread
-constexpr int kRsTile = kRsThreads * kRsItems;        // 4096 keys per block
 constexpr int kRsBins = 256;
+static_assert(kRsThreads == kRsBins, "one thread per digit in the scatter's digit scan");
+
+// Keys per thread and per block: the scatter stages a block's keys and values in shared memory,
+// 16 KB + 16 KB for 32-bit keys, 16 KB + 8 KB for 64-bit ones.
+template <class K>
+struct RsCfg {
+  static constexpr int kItems = sizeof(K) == 8 ? 8 : 16;
+  static constexpr int kTile = kRsThreads * kItems;
+};
+constexpr int kRsMinTile = RsCfg<uint64_t>::kTile;  // workspace sizes hold for either key width
 
 __device__ __forceinline__ int64_t live_count(const int64_t* n_dev, int64_t capacity) {
   const int64_t n = *n_dev;
@@ -186,14 +194,15 @@ template <class K>
 __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restrict__ keys,
                                                                 const int64_t* __restrict__ n_dev, int64_t capacity,
                                                                 int shift, int nblocks, uint32_t* __restrict__ hist) {
+  constexpr int kTile = RsCfg<K>::kTile;
   __shared__ uint32_t h[kRsWarps][kRsBins];
   for (int k = threadIdx.x; k < kRsWarps * kRsBins; k += kRsThreads) (&h[0][0])[k] = 0;
   __syncthreads();
   const int64_t n = live_count(n_dev, capacity);
-  const int64_t lo = (int64_t)blockIdx.x * kRsTile;
+  const int64_t lo = (int64_t)blockIdx.x * kTile;
   const int warp = threadIdx.x >> 5;
   if (lo < n) {
-    const int64_t hi = min(lo + (int64_t)kRsTile, n);
+    const int64_t hi = min(lo + (int64_t)kTile, n);
     for (int64_t i = lo + threadIdx.x; i < hi; i += kRsThreads) {
       const uint32_t d = (uint32_t)(keys[i] >> shift) & 0xffu;
       atomicAdd(&h[warp][d], 1u);
@@ -208,28 +217,36 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restr
   }
 }
 
-// Stable scatter: warp w ranks the keys of its contiguous 512-key segment in order, using warp-private
-// digit counters; a per-digit exclusive scan over the warps then places each warp's keys after those of
-// the earlier warps, and the scanned histogram places the block after the earlier blocks.
+// Stable scatter: warp w ranks the keys of its contiguous segment in order, using warp-private digit
+// counters; per digit, an exclusive scan over the warps places each warp's keys after those of the
+// earlier warps.  The block's keys and values are then laid out digit-major in shared memory and
+// written out by consecutive threads, so each digit's run of the block goes to consecutive
+// addresses (after the scanned histogram's offset for the block).
 template <class K>
 __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, const int64_t* __restrict__ n_dev, int64_t capacity, int shift, int nblocks,
     const uint32_t* __restrict__ offs) {
+  constexpr int kItems = RsCfg<K>::kItems, kTile = RsCfg<K>::kTile;
   __shared__ uint32_t cnt[kRsWarps][kRsBins];
+  __shared__ uint32_t dstart[kRsBins];  // first slot of each digit in the block's digit-major layout
+  __shared__ uint32_t gbase[kRsBins];   // output position of that slot
+  __shared__ uint32_t wtot[kRsWarps];
+  __shared__ K skey[kTile];
+  __shared__ uint32_t sval[kTile];
   const int64_t n = live_count(n_dev, capacity);
-  const int64_t lo = (int64_t)blockIdx.x * kRsTile;
+  const int64_t lo = (int64_t)blockIdx.x * kTile;
   if (lo >= n) return;  // uniform per block
   for (int k = threadIdx.x; k < kRsWarps * kRsBins; k += kRsThreads) (&cnt[0][0])[k] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int64_t seg = lo + (int64_t)warp * (32 * kRsItems);
-  K key[kRsItems];
-  uint32_t val[kRsItems];
-  uint32_t rank[kRsItems];
+  const int64_t seg = lo + (int64_t)warp * (32 * kItems);
+  K key[kItems];
+  uint32_t val[kItems];
+  uint32_t rank[kItems];
 #pragma unroll
-  for (int j = 0; j < kRsItems; ++j) {
+  for (int j = 0; j < kItems; ++j) {
     const int64_t i = seg + j * 32 + lane;
     const bool ok = i < n;
     key[j] = ok ? kin[i] : (K)0;
@@ -243,26 +260,49 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive scan over warps, plus the block's global offset
-  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) {
-    uint32_t run = offs[(int64_t)d * nblocks + blockIdx.x];
+  {
+    // thread d: exclusive scan of digit d over the warps, then of the block's digit totals over d
+    const int d = threadIdx.x;
+    uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) {
       const uint32_t c = cnt[w][d];
-      cnt[w][d] = run;
-      run += c;
+      cnt[w][d] = tot;
+      tot += c;
     }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    gbase[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+    __syncthreads();
+    uint32_t before = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) before += (w < warp) ? wtot[w] : 0u;
+    dstart[d] = before + incl - tot;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kRsItems; ++j) {
+  for (int j = 0; j < kItems; ++j) {
     const int64_t i = seg + j * 32 + lane;
     if (i < n) {
       const uint32_t d = (uint32_t)(key[j] >> shift) & 0xffu;
-      const uint32_t pos = cnt[warp][d] + rank[j];
-      kout[pos] = key[j];
-      vout[pos] = val[j];
+      const uint32_t s = dstart[d] + cnt[warp][d] + rank[j];
+      skey[s] = key[j];
+      sval[s] = val[j];
     }
+  }
+  __syncthreads();
+  const int count = (int)min((int64_t)kTile, n - lo);
+  for (int s = threadIdx.x; s < count; s += kRsThreads) {
+    const K k = skey[s];
+    const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
+    const uint32_t pos = gbase[d] + ((uint32_t)s - dstart[d]);
+    kout[pos] = k;
+    vout[pos] = sval[s];
   }
 }
 
@@ -340,7 +380,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_
 }
 
 size_t radix_workspace_bytes(int64_t capacity) {
-  const int64_t nblocks = (capacity + kRsTile - 1) / kRsTile;
+  const int64_t nblocks = (capacity + kRsMinTile - 1) / kRsMinTile;
   const int64_t hist = (int64_t)kRsBins * (nblocks > 0 ? nblocks : 1);
   size_t b = sizeof(uint32_t) * (size_t)hist;  // histogram, scanned in place
   b = (b + 255) & ~(size_t)255;
@@ -353,7 +393,7 @@ template <class K>
 cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint32_t* vals_out,
                               int64_t capacity, const int64_t* n_dev, int bits, void* ws, K** keys_result,
                               cudaStream_t st) {
-  const int64_t nb64 = (capacity + kRsTile - 1) / kRsTile;
+  const int64_t nb64 = (capacity + RsCfg<K>::kTile - 1) / RsCfg<K>::kTile;
   const int nblocks = (int)(nb64 > 0 ? nb64 : 1);
   const int64_t hist_n = (int64_t)kRsBins * nblocks;
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws);

@@ -64,9 +64,7 @@ struct WarpPix {
 struct HalfStage {
   float4 a[32];
   float4 b[32];
-  float c2[32];
-  uint32_t pos[32];
-  uint32_t rec[32];
+  uint4 x[32];  // (colour b bits, list position, record, 0)
 };
 
 // Stage the chunk [lo, hi) of the tile list: every lane tests one entry against both halves' blocks
@@ -92,13 +90,14 @@ __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const fl
     const float4 b = __ldg(&proj[VN + r]);
     const float c2 = __ldg(&proj[2 * VN + r]).x;
     const uint32_t pos = idx - tile_start;
+    const uint4 x = make_uint4(__float_as_uint(c2), pos, r, 0u);
     if (hit0) {
       const int k = __popc(m0 & lt);
-      st[0].a[k] = a; st[0].b[k] = b; st[0].c2[k] = c2; st[0].pos[k] = pos; st[0].rec[k] = r;
+      st[0].a[k] = a; st[0].b[k] = b; st[0].x[k] = x;
     }
     if (hit1) {
       const int k = __popc(m1 & lt);
-      st[1].a[k] = a; st[1].b[k] = b; st[1].c2[k] = c2; st[1].pos[k] = pos; st[1].rec[k] = r;
+      st[1].a[k] = a; st[1].b[k] = b; st[1].x[k] = x;
     }
   }
   __syncwarp();
@@ -152,12 +151,13 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
       const bool b0 = k0 && !s0, b1 = k1 && !s1;
       // a pixel that does not blend gets weight 0, which leaves its colour unchanged exactly
       const float2 w = __fmul2_rn(make_float2(b0 ? f.alpha.x : 0.0f, b1 ? f.alpha.y : 0.0f), T);
-      const float c2 = mine.c2[t];
+      const uint4 x = mine.x[t];
+      const float c2 = __uint_as_float(x.x);
       Cr = __ffma2_rn(w, make_float2(b.z, b.z), Cr);
       Cg = __ffma2_rn(w, make_float2(b.w, b.w), Cg);
       Cb = __ffma2_rn(w, make_float2(c2, c2), Cb);
       T = make_float2(b0 ? Tn.x : T.x, b1 ? Tn.y : T.y);
-      const uint32_t p1 = mine.pos[t] + 1u;
+      const uint32_t p1 = x.y + 1u;
       last0 = b0 ? p1 : last0;
       last1 = b1 ? p1 : last1;
       cnt0 += b0 ? 1u : 0u;
@@ -340,9 +340,10 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
       if (t < cnt) {
         const float4 a = mine.a[t];
         const float4 b = mine.b[t];
-        const float c2 = mine.c2[t];
-        const uint32_t pos = mine.pos[t];
-        rr = mine.rec[t];
+        const uint4 x = mine.x[t];
+        const float c2 = __uint_as_float(x.x);
+        const uint32_t pos = x.y;
+        rr = x.z;
         const float dx = __fsub_rn(fx, a.x);
         const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
         FragPair f;
