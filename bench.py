@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=4)
     ap.add_argument("--tile", default="auto", help="screen tile WxH, or auto (time the candidates)")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time the 2,000- and 200k-Gaussian render cases and the 16-view batch, GPU and "
+                         "oracle (adds a 'configs' object to the line)")
     ap.add_argument("--small", action="store_true",
                     help="50-frame video (~0.4 M Gaussians) for profiler captures; not a bench value")
     return ap.parse_args()
@@ -53,15 +56,18 @@ def parse_args():
 # ------------------------------------------------------------------------------------------------
 # distributed replicas
 # ------------------------------------------------------------------------------------------------
-def dist_init():
+def dist_init(backend: str = "nccl"):
+    """Replicas: one process per GPU (RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from the launcher).
+    The only collectives are the barriers around the timed region and the max of the step times."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -76,9 +82,15 @@ def max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ms_per_step_by_rank_max: float, ws: int) -> float:
+    """Whole-job throughput of N replicas: every rank runs one step per ms_max (the slowest rank)."""
+    return ws * 1000.0 / ms_per_step_by_rank_max
 
 
 # ------------------------------------------------------------------------------------------------
@@ -293,6 +305,82 @@ def measured_peaks():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# the other workloads (parity-test cases), timed on request
+# ------------------------------------------------------------------------------------------------
+def _time_render(g_params, n, sh_deg, cams, sizes, dev, reps=20):
+    """ms per render forward + backward (slice_project .. slice_project_bwd) of one batch."""
+    import torch
+    from paper_2510_01119_gb300 import rasterizer as R
+    rast = R.Rasterizer(n, sh_deg, 0, sizes, device=dev)
+    rast.forward(g_params, cams)
+    rast._alloc_bins(int(1.2 * int(rast.n_inst.item())) + 4096)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    up = (torch.rand(rast.img.numel(), device=dev, generator=gen) - 0.5) * 1e-3
+    for _ in range(3):
+        rast.forward(g_params, cams, check_capacity=False)
+        rast.backward(g_params, cams, up)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rast.forward(g_params, cams, check_capacity=False)
+        rast.backward(g_params, cams, up)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, int(rast.n_inst.item())
+
+
+def _time_oracle(g, cam, n_pix, threads):
+    """Oracle seconds for projection + forward + backward of n_pix pixels (all if None)."""
+    import oracle
+    oracle.set_threads(threads)
+    W, H = int(cam["W"]), int(cam["H"])
+    pix = None if n_pix is None else np.random.default_rng(0).integers(0, W * H, n_pix).astype(np.int32)
+    m = W * H if pix is None else n_pix
+    t0 = time.perf_counter()
+    P = oracle.project(g, cam)
+    oracle.render(P, cam, pix=pix)
+    oracle.render_bwd(g, cam, np.full((m, 3), 1e-3), pix=pix)
+    return time.perf_counter() - t0
+
+
+def run_configs(dev, wl):
+    import torch
+
+    import oracle
+    import synth
+    from paper_2510_01119_gb300 import rasterizer as R
+    oracle.build()
+    nthr = oracle.max_threads()
+    out = {}
+    # 2,000 Gaussians, 128x96, one view at t = 0.5
+    g0 = synth.gaussians_uniform(0)
+    cam0 = synth.camera(128, 96, 60.0, time=0.5)
+    ms, inst = _time_render(R.pack_params(g0, dev), 2000, 0, R.cameras_tensor([cam0], dev), [(128, 96)], dev, 50)
+    out["render_2k_128x96"] = {"gpu_ms_fwd_bwd": ms, "instances": inst,
+                               "oracle_s_1thread": _time_oracle(g0, cam0, None, 1),
+                               "oracle_s_all_threads": _time_oracle(g0, cam0, None, nthr), "threads": nthr}
+    # 200k Gaussians on surfaces, SH degree 3, one 960x540 arc view
+    g1 = synth.gaussians_surfaces(1)
+    cam1 = synth.arc_camera(57, 200, 960, 540, time=0.37)
+    ms, inst = _time_render(R.pack_params(g1, dev), g1["mean4"].shape[0], 3, R.cameras_tensor([cam1], dev),
+                            [(960, 540)], dev)
+    npx = 256
+    s1 = _time_oracle(g1, cam1, npx, nthr)
+    out["render_200k_sh3_960x540"] = {"gpu_ms_fwd_bwd": ms, "instances": inst,
+                                      "oracle_s_all_threads_extrapolated": s1 * (960 * 540) / npx,
+                                      "oracle_sample": f"{npx} pixels, extrapolated linearly", "threads": nthr}
+    # the pruned 1.13M scene, 16 views at distinct times: 8 x 480x270 + 8 x 960x540, one launch each
+    frames = np.random.default_rng(7).choice(N_FRAMES, 16, replace=False)
+    sizes = [HALF] * 8 + [FULL] * 8
+    cams = R.cameras_tensor([synth.arc_camera(int(f), N_FRAMES, W, H) for f, (W, H) in zip(frames, sizes)], dev)
+    ms, inst = _time_render(wl["params"], wl["n"], 0, cams, sizes, dev)
+    out["render_1M_16views"] = {"gpu_ms_fwd_bwd": ms, "instances": inst, "prune_ms": wl["prune_ms"]}
+    oracle.set_threads(nthr)
+    return out
 
 
 # ------------------------------------------------------------------------------------------------
@@ -521,7 +609,7 @@ def run_ours(args, ws, rank, local):
     else:
         roofline = {"kernel": dominant, "bound": "hbm", "ms_per_launch": dom_ms, **hbm}
 
-    value = ws * 1000.0 / ms_max
+    value = aggregate(ms_max, ws)
     line = {
         "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -546,6 +634,8 @@ def run_ours(args, ws, rank, local):
     }
     if args.small:
         line["config"]["workload"] = "train_step_small_profile_only"
+    if args.configs and rank == 0:
+        line["configs"] = run_configs(dev, wl)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.small:
         import oracle
         oracle.build()
