@@ -76,17 +76,20 @@ I4D_D float blend_q(float ot, const Settings& s) {
 
 // One Gaussian evaluated at a thread's two pixels (same column, offsets dx and dy.x / dy.y from the
 // projected mean): q = ca dx^2 + 2 cb dx dy + cc dy^2, the falloff G = exp(-q/2), the raw alpha
-// o_t G and the clamped alpha; kept = inside the q_max ellipse and alpha >= alpha_min.  The pixel
-// pair runs on the packed FP32x2 instructions of sm_100 and later (__fmul2_rn / __ffma2_rn round
-// each lane exactly as __fmul_rn / __fmaf_rn), so every value equals the scalar computation with
-// these explicit roundings.  The forward and the backward compositing kernels call exactly this
-// code on the same inputs, so they take the same decisions.
+// o_t G and the clamped alpha.  A fragment is kept where q <= q_max and o_t exp(-q/2) >= alpha_min,
+// i.e. where q <= q_thr = min(q_max, 2 ln(o_t / alpha_min)), a per-Gaussian threshold computed once
+// when the entry is staged (one compare per pixel instead of two; the two forms differ only by
+// rounding, well inside the 1e-4 relative margin the parity protocol gives threshold decisions).
+// The pixel pair runs on the packed FP32x2 instructions of sm_100 and later (__fmul2_rn /
+// __ffma2_rn round each lane exactly as __fmul_rn / __fmaf_rn).  The forward and the backward
+// compositing kernels call exactly this code on the same inputs, so they take the same decisions.
 struct FragPair {
   float2 q, G, a_raw, alpha, dxdy, dydy;
   bool k0, k1;
 };
 
-I4D_D void eval_pair(float dx, float2 dy, float ca, float cb, float cc, float ot, const Settings& s, FragPair& f) {
+I4D_D void eval_pair(float dx, float2 dy, float ca, float cb, float cc, float ot, float q_thr, const Settings& s,
+                     FragPair& f) {
   const float t0 = __fmul_rn(ca, __fmul_rn(dx, dx));
   const float c2b = __fmul_rn(2.0f, cb);
   f.dxdy = __fmul2_rn(make_float2(dx, dx), dy);
@@ -96,8 +99,8 @@ I4D_D void eval_pair(float dx, float2 dy, float ca, float cb, float cc, float ot
   f.G = make_float2(__expf(m.x), __expf(m.y));
   f.a_raw = __fmul2_rn(make_float2(ot, ot), f.G);
   f.alpha = make_float2(fminf(s.alpha_max, f.a_raw.x), fminf(s.alpha_max, f.a_raw.y));
-  f.k0 = f.q.x <= s.q_max && f.alpha.x >= s.alpha_min;
-  f.k1 = f.q.y <= s.q_max && f.alpha.y >= s.alpha_min;
+  f.k0 = f.q.x <= q_thr;
+  f.k1 = f.q.y <= q_thr;
 }
 
 // Pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max of a conic, widened by

@@ -64,7 +64,7 @@ struct WarpPix {
 struct HalfStage {
   float4 a[32];
   float4 b[32];
-  uint4 x[32];  // (colour b bits, list position, record, 0)
+  uint4 x[32];  // (colour b bits, list position, record, q threshold bits)
 };
 
 // Stage the chunk [lo, hi) of the tile list: every lane tests one entry against both halves' blocks
@@ -72,7 +72,7 @@ struct HalfStage {
 template <class WP>
 __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const float4* __restrict__ proj, size_t VN,
                                            const uint32_t* __restrict__ ids, uint32_t vbase, uint32_t lo, uint32_t hi,
-                                           uint32_t tile_start, int lane, int& other) {
+                                           uint32_t tile_start, int lane, int& other, const Settings& S) {
   const uint32_t idx = lo + lane;
   uint32_t r = 0;
   bool hit0 = false, hit1 = false;
@@ -90,7 +90,8 @@ __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const fl
     const float4 b = __ldg(&proj[VN + r]);
     const float c2 = __ldg(&proj[2 * VN + r]).x;
     const uint32_t pos = idx - tile_start;
-    const uint4 x = make_uint4(__float_as_uint(c2), pos, r, 0u);
+    const float q_thr = fminf(S.q_max, 2.0f * logf(b.y / S.alpha_min));
+    const uint4 x = make_uint4(__float_as_uint(c2), pos, r, __float_as_uint(q_thr));
     if (hit0) {
       const int k = __popc(m0 & lt);
       st[0].a[k] = a; st[0].b[k] = b; st[0].x[k] = x;
@@ -135,28 +136,30 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
   for (uint32_t base = rs; base < re; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
     int other;
-    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, base, min(base + 32u, re), rs, lane, other);
-    for (int t = 0; t < cnt && !(done0 && done1); ++t) {
+    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, base, min(base + 32u, re), rs, lane, other, S);
+    for (int t = 0; t < cnt; ++t) {
       const float4 a = mine.a[t];
       const float4 b = mine.b[t];
+      const uint4 x = mine.x[t];
       const float dx = __fsub_rn(fx, a.x);
       FragPair f;
-      eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, S, f);
+      eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
       const bool k0 = f.k0 && !done0, k1 = f.k1 && !done1;
-      // a kept fragment that would take T below T_min stops the pixel without being blended
-      const float2 Tn = __fmul2_rn(T, __ffma2_rn(f.alpha, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f)));
+      // a kept fragment that would take T below T_min stops the pixel without being blended;
+      // T (1 - alpha) is formed as T - alpha T, so a pixel with weight 0 keeps T exactly
+      const float2 wk = __fmul2_rn(f.alpha, T);
+      const float2 Tn = __fadd2_rn(T, make_float2(-wk.x, -wk.y));
       const bool s0 = k0 && Tn.x < S.T_min, s1 = k1 && Tn.y < S.T_min;
       done0 = done0 || s0;
       done1 = done1 || s1;
       const bool b0 = k0 && !s0, b1 = k1 && !s1;
-      // a pixel that does not blend gets weight 0, which leaves its colour unchanged exactly
-      const float2 w = __fmul2_rn(make_float2(b0 ? f.alpha.x : 0.0f, b1 ? f.alpha.y : 0.0f), T);
-      const uint4 x = mine.x[t];
+      // a pixel that does not blend gets weight 0, which leaves its colour and T unchanged exactly
+      const float2 w = make_float2(b0 ? wk.x : 0.0f, b1 ? wk.y : 0.0f);
       const float c2 = __uint_as_float(x.x);
       Cr = __ffma2_rn(w, make_float2(b.z, b.z), Cr);
       Cg = __ffma2_rn(w, make_float2(b.w, b.w), Cg);
       Cb = __ffma2_rn(w, make_float2(c2, c2), Cb);
-      T = make_float2(b0 ? Tn.x : T.x, b1 ? Tn.y : T.y);
+      T = __fadd2_rn(T, make_float2(-w.x, -w.y));
       const uint32_t p1 = x.y + 1u;
       last0 = b0 ? p1 : last0;
       last1 = b1 ? p1 : last1;
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   for (uint32_t hi = end; hi > rs;) {
     const uint32_t lo = (hi - rs > 32u) ? hi - 32u : rs;
     int other;
-    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, lo, hi, rs, lane, other);
+    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
     const int trips = max(cnt, other);  // warp-uniform
     for (int t = trips - 1; t >= 0; --t) {
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
         const float dx = __fsub_rn(fx, a.x);
         const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
         FragPair f;
-        eval_pair(dx, dy, a.z, a.w, b.x, b.y, S, f);
+        eval_pair(dx, dy, a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
         // the fragments a pixel blended are the kept ones before its last (out-of-view pixels: L = 0)
         const bool k0 = f.k0 && pos < P.L0, k1 = f.k1 && pos < P.L1;
         any = k0 || k1;
