@@ -342,6 +342,16 @@ I4D_API void i4d_profile_reset(void);
 I4D_API int32_t i4d_profile_count(void);
 I4D_API int32_t i4d_profile_read(int32_t k, char* name, int32_t name_len, double* total_ms, int64_t* launches);
 
+/*
+ * i4d_measure_fp32_peak -- the FP32 roofline's denominator, measured: a kernel of packed FP32x2
+ * FMA chains (8 independent chains per thread, 256 threads per block, blocks_per_sm blocks per SM,
+ * iters iterations) is timed with CUDA events on `stream`; *tflops = FLOPs (an FMA counts 2) per
+ * second / 1e12.  Synchronises the stream.  The paper has no counterpart: it is the measured peak
+ * that the compositing kernels' FP32 roofline divides by.  Errors: I4D_ERR_ARG (tflops NULL,
+ * blocks_per_sm outside 1..64, iters < 1), I4D_ERR_CUDA.
+ */
+I4D_API int32_t i4d_measure_fp32_peak(int32_t blocks_per_sm, int32_t iters, double* tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,7 @@ _SIGS = {
     "i4d_profile_count": (c_i32, []),
     "i4d_profile_read": (c_i32, [c_i32, ctypes.c_char_p, c_i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(c_i64)]),
+    "i4d_measure_fp32_peak": (c_i32, [c_i32, c_i32, ctypes.POINTER(ctypes.c_double), c_vp]),
 }
 
 
@@ -250,6 +251,14 @@ def profile_enable(on: bool = True) -> None:
 
 def profile_reset() -> None:
     load().i4d_profile_reset()
+
+
+def i4d_measure_fp32_peak(blocks_per_sm: int = 8, iters: int = 20000, stream=None) -> float:
+    """Measured FP32 FMA throughput of this GPU in TFLOP/s (packed-FMA chains; syncs the stream)."""
+    out = ctypes.c_double()
+    check(load().i4d_measure_fp32_peak(int(blocks_per_sm), int(iters), ctypes.byref(out), stream_ptr(stream)),
+          "i4d_measure_fp32_peak")
+    return float(out.value)
 
 
 def profile_read() -> dict:

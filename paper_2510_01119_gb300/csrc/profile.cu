@@ -83,6 +83,27 @@ ProfScope::~ProfScope() {
   g_entries[slot_].pending.emplace_back(start_, end);
 }
 
+namespace {
+
+// FP32 FMA throughput probe: every thread runs 8 independent packed-FMA chains (16 FMAs per
+// iteration per thread), so issue and the FMA pipes, not latency, set the rate.
+__global__ void __launch_bounds__(256) fp32_peak_kernel(int iters, float seed, float* __restrict__ out) {
+  float2 acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = make_float2(seed + (float)k, seed - (float)k);
+  const float2 m = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = __ffma2_rn(acc[k], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += acc[k].x + acc[k].y;
+  if (s == 1234.5f) out[0] = s;  // never true for these inputs; keeps the chains live
+}
+
+}  // namespace
+
 }  // namespace i4d
 
 using namespace i4d;
@@ -107,6 +128,34 @@ void i4d_profile_reset(void) {
 int32_t i4d_profile_count(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   return (int32_t)g_entries.size();
+}
+
+int32_t i4d_measure_fp32_peak(int32_t blocks_per_sm, int32_t iters, double* tflops, void* stream) {
+  if (!tflops || blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1) return I4D_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return I4D_ERR_CUDA;
+  float* sink = nullptr;
+  if (cudaMallocAsync(&sink, sizeof(float), st) != cudaSuccess) return I4D_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int grid = sms * blocks_per_sm;
+  fp32_peak_kernel<<<grid, 256, 0, st>>>(iters / 10 + 1, 1.0f, sink);  // warm-up
+  cudaEventRecord(e0, st);
+  fp32_peak_kernel<<<grid, 256, 0, st>>>(iters, 1.0f, sink);
+  cudaEventRecord(e1, st);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(sink, st);
+  if (err != cudaSuccess || ms <= 0.0f) return I4D_ERR_CUDA;
+  const double flops = (double)grid * 256.0 * (double)iters * 8.0 * 2.0 * 2.0;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return I4D_OK;
 }
 
 int32_t i4d_profile_read(int32_t k, char* name, int32_t name_len, double* total_ms, int64_t* launches) {

@@ -156,3 +156,14 @@ def test_prune_depth_video_matches_oracle(dev, orc):
     assert same_rep.mean() > 0.99
     assert np.allclose(got["xyz"][gi][same_rep], want["centroid"][wi][same_rep], atol=1e-4)
     assert np.allclose(got["rgb"][gi][same_rep], want["rgb"][wi][same_rep], atol=1e-5)
+
+
+def test_fp32_peak_probe_is_plausible(dev):
+    """The measured FP32 FMA throughput (the compositing roofline's denominator) lies between half
+    and 1.1x of SMs x 128 lanes x 2 FLOP x the fastest clock a GB300 runs (2.1 GHz)."""
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nominal = sms * 128 * 2 * 2.1e9 / 1e12
+    peak = L.i4d_measure_fp32_peak()
+    assert 0.5 * nominal < peak < 1.1 * nominal, (peak, nominal)
