@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=4)
     ap.add_argument("--tile", default="auto", help="screen tile WxH, or auto (time the candidates)")
+    ap.add_argument("--loss", choices=["l1+dssim", "l1"], default="l1+dssim",
+                    help="photometric loss: the standard 3DGS (1 - 0.2) L1 + 0.2 D-SSIM, or L1 alone")
     ap.add_argument("--configs", action="store_true",
                     help="also time the 2,000- and 200k-Gaussian render cases and the 16-view batch, GPU and "
                          "oracle (adds a 'configs' object to the line)")
@@ -482,17 +484,18 @@ def run_ours(args, ws, rank, local):
     V = len(sizes)
     total_steps = args.warmup + args.steps
     batches = step_batches(total_steps + args.profile_steps)
+    dssim = T.DSSIM_LAMBDA if args.loss == "l1+dssim" else 0.0
     tune = None
     if args.tile == "auto":
         from paper_2510_01119_gb300 import autotune
         fa, fb = batches[0]
         cams0 = torch.cat([wl["cam_bank"][FULL][torch.as_tensor(fa)], wl["cam_bank"][HALF][torch.as_tensor(fb)]])
         tgt0 = torch.cat([wl["bank"][FULL][torch.as_tensor(fa)].reshape(-1), wl["bank"][HALF][torch.as_tensor(fb)].reshape(-1)])
-        tile, tune = autotune.tune_tile(wl["params"], n, sizes, cams0, tgt0)
+        tile, tune = autotune.tune_tile(wl["params"], n, sizes, cams0, tgt0, dssim=dssim)
     else:
         tile = tuple(int(x) for x in args.tile.split("x"))
     step = T.TrainStep(wl["params"], n, 0, 0, sizes, steps=max(total_steps, 2000), loss_kind=L.LOSS_L1,
-                       capacity=16 * n, tile=tile)
+                       capacity=16 * n, tile=tile, dssim=dssim)
     fullpix, halfpix = 3 * FULL[0] * FULL[1], 3 * HALF[0] * HALF[1]
     tgt_full = step.target[:N_FULL * fullpix].view(N_FULL, fullpix)
     tgt_half = step.target[N_FULL * fullpix:].view(N_HALF, halfpix)
@@ -584,6 +587,7 @@ def run_ours(args, ws, rank, local):
     per_step = {k: v[0] / args.profile_steps for k, v in prof.items()}
     launches_per_step = sum(KERNELS_PER_SCOPE.get(k, 1) * v[1] for k, v in prof.items()) / args.profile_steps
     launches_per_step += 1  # the Adam step-counter kernel
+    launches_per_step += 1 if dssim > 0 else 0  # the loss finishing kernel
     tot = sum(per_step.values())
     dominant = max(per_step, key=per_step.get)
     dom_launches = prof[dominant][1] / args.profile_steps
@@ -620,7 +624,8 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": "train_step_1M_8views", "n_gaussians": n, "n_dynamic": wl["n_dynamic"],
                    "views": "4x960x540+4x480x270", "tile": f"{tile[0]}x{tile[1]}",
                    "tile_ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tune.items()} if tune else None,
-                   "init": "heuristic, 3-NN spatial scale", "loss": "L1",
+                   "init": "heuristic, 3-NN spatial scale",
+                   "loss": "(1 - 0.2) L1 + 0.2 D-SSIM" if dssim > 0 else "L1",
                    "graph": not args.eager, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (params 90 MB + records 430 MB + bins per step)",
                    "instances": I, "visible_records": R_vis, "pixels": P},

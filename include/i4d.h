@@ -231,6 +231,24 @@ I4D_API int32_t i4d_render_bwd_noalloc(const i4d_gaussians* g, const i4d_views* 
 I4D_API int32_t i4d_loss(const float* img, const float* target, int64_t count, int32_t kind, float* dL_dimg,
                  float* loss_out, void* stream);
 
+/*
+ * i4d_photometric_loss -- the training loss with the loss weights of standard 3D Gaussian splatting
+ * that Sec. 4.1 adopts: (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM), lambda_dssim = 0.2 there.
+ * L1 is the mean absolute error over every pixel and channel of all views; SSIM is computed per
+ * channel with an 11x11 Gaussian window (sigma 1.5, weights summing to 1) centred on every pixel,
+ * zeros outside the image, C1 = 0.01^2, C2 = 0.03^2, and averaged over every pixel and channel of
+ * all views (the SSIM of Tables 1-4, per view, when the batch holds one view).
+ *   views     host; img, target DEVICE, the planar multi-view image layout
+ *   dL_dimg   DEVICE out, same layout: the gradient of the loss (overwritten, not accumulated)
+ *   loss_out  DEVICE out, 1 float; ssim_out DEVICE out, 1 float (nullable): the mean SSIM
+ *   ws        DEVICE scratch of i4d_photometric_loss_workspace_size(views) bytes (9 floats per pixel)
+ * Errors: I4D_ERR_ARG (bad views, lambda outside [0, 1], NULL pointers), I4D_ERR_WORKSPACE.
+ */
+I4D_API size_t i4d_photometric_loss_workspace_size(const i4d_views* views);
+I4D_API int32_t i4d_photometric_loss(const i4d_views* views, const float* img, const float* target,
+                                     float lambda_dssim, float* dL_dimg, float* loss_out, float* ssim_out, void* ws,
+                                     size_t ws_bytes, void* stream);
+
 /* i4d_psnr -- 10 log10(1 / MSE) over count floats in [0, 1] (the PSNR of Tables 1-4). */
 I4D_API int32_t i4d_psnr(const float* img, const float* target, int64_t count, float* psnr_out, void* stream);
 

@@ -76,6 +76,9 @@ _SIGS = {
                                c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "i4d_loss": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "i4d_psnr": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "i4d_photometric_loss_workspace_size": (c_sz, [ctypes.POINTER(Views)]),
+    "i4d_photometric_loss": (c_i32, [ctypes.POINTER(Views), c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_sz,
+                                     c_vp]),
     "i4d_adam_step": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(AdamGroup), c_i32, c_vp, c_f, c_f, c_f,
                               c_vp]),
     "i4d_prune_workspace_size": (c_sz, [c_i64, c_i64]),
@@ -204,6 +207,17 @@ def i4d_render_bwd(g: Gaussians, views: Views, cams, settings, proj, touched, id
 def i4d_loss(img, target, kind: int, dL_dimg, loss_out, stream=None):
     check(load().i4d_loss(ptr(img), ptr(target), img.numel(), int(kind), ptr(dL_dimg), ptr(loss_out),
                           stream_ptr(stream)), "i4d_loss")
+
+
+def i4d_photometric_loss_workspace_size(views: Views) -> int:
+    return int(load().i4d_photometric_loss_workspace_size(ctypes.byref(views)))
+
+
+def i4d_photometric_loss(views: Views, img, target, lambda_dssim: float, dL_dimg, loss_out, ssim_out, ws,
+                         stream=None):
+    check(load().i4d_photometric_loss(ctypes.byref(views), ptr(img), ptr(target), float(lambda_dssim), ptr(dL_dimg),
+                                      ptr(loss_out), ptr(ssim_out), ptr(ws), ws.numel() * ws.element_size(),
+                                      stream_ptr(stream)), "i4d_photometric_loss")
 
 
 def i4d_psnr(img, target, psnr_out, stream=None):

@@ -15,13 +15,13 @@ TILES = [(16, 16), (16, 8), (32, 16), (32, 8), (8, 8)]
 
 
 def tune_tile(params: torch.Tensor, n: int, sizes, cams: torch.Tensor, target: torch.Tensor, steps: int = 3,
-              tiles=TILES, log=None):
+              tiles=TILES, log=None, dssim: float = 0.0):
     """Time `steps` eager training steps per tile shape on copies of the parameters; returns
     (best tile, {tile: ms per step})."""
     res = {}
     for tile in tiles:
         p = params.clone()
-        st = T.TrainStep(p, n, 0, 0, sizes, steps=1000, loss_kind=L.LOSS_L1, tile=tile)
+        st = T.TrainStep(p, n, 0, 0, sizes, steps=1000, loss_kind=L.LOSS_L1, tile=tile, dssim=dssim)
         st.cams.copy_(cams)
         st.target.copy_(target)
         st.rast.forward(p, st.cams, check_capacity=True)

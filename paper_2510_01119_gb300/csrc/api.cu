@@ -185,6 +185,24 @@ int32_t i4d_loss(const float* img, const float* target, int64_t count, int32_t k
   return cuda_status(launch_loss(img, target, count, kind, dL_dimg, loss_out, (cudaStream_t)stream));
 }
 
+size_t i4d_photometric_loss_workspace_size(const i4d_views* views) {
+  ViewTable vt;
+  if (!make_view_table(views, vt)) return 0;
+  return photometric_workspace_bytes(vt);
+}
+
+int32_t i4d_photometric_loss(const i4d_views* views, const float* img, const float* target, float lambda_dssim,
+                             float* dL_dimg, float* loss_out, float* ssim_out, void* ws, size_t ws_bytes,
+                             void* stream) {
+  ViewTable vt;
+  if (!make_view_table(views, vt)) return I4D_ERR_ARG;
+  if (!(lambda_dssim >= 0.0f && lambda_dssim <= 1.0f) || !img || !target || !dL_dimg || !loss_out || !ws)
+    return I4D_ERR_ARG;
+  if (ws_bytes < photometric_workspace_bytes(vt)) return I4D_ERR_WORKSPACE;
+  return cuda_status(launch_photometric_loss(vt, img, target, lambda_dssim, dL_dimg, loss_out, ssim_out, ws,
+                                             (cudaStream_t)stream));
+}
+
 int32_t i4d_psnr(const float* img, const float* target, int64_t count, float* psnr_out, void* stream) {
   if (count < 0 || !psnr_out || (count > 0 && (!img || !target))) return I4D_ERR_ARG;
   return cuda_status(launch_psnr(img, target, count, psnr_out, (cudaStream_t)stream));

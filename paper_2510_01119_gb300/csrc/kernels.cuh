@@ -44,6 +44,11 @@ cudaError_t launch_loss(const float* img, const float* target, int64_t count, in
                         float* loss_out, cudaStream_t st);
 cudaError_t launch_psnr(const float* img, const float* target, int64_t count, float* psnr_out, cudaStream_t st);
 
+// (1 - lambda) L1 + lambda (1 - SSIM) over all views, with its gradient
+size_t photometric_workspace_bytes(const ViewTable& vt);
+cudaError_t launch_photometric_loss(const ViewTable& vt, const float* img, const float* target, float lam,
+                                    float* dL_dimg, float* loss_out, float* ssim_out, void* ws, cudaStream_t st);
+
 struct AdamGroups {
   int n;
   int64_t begin[I4D_MAX_ADAM_GROUPS], end[I4D_MAX_ADAM_GROUPS];

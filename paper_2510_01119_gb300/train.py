@@ -40,11 +40,17 @@ def adam_groups(n: int, sh_deg: int, steps: int, lr: dict = None):
     return groups
 
 
+# the D-SSIM weight of the standard 3D Gaussian splatting loss (Sec. 4.1 adopts its loss weights)
+DSSIM_LAMBDA = 0.2
+
+
 class TrainStep:
-    """Device-resident training step for a fixed batch layout (view sizes) of n Gaussians."""
+    """Device-resident training step for a fixed batch layout (view sizes) of n Gaussians.  The loss is
+    (1 - dssim) L1 + dssim (1 - SSIM) when dssim > 0, else i4d_loss of loss_kind (L1 or MSE)."""
 
     def __init__(self, params: torch.Tensor, n: int, sh_deg: int, mode: int, sizes, steps: int,
-                 loss_kind: int = L.LOSS_L1, capacity: int = None, tile=(16, 16), lr: dict = None):
+                 loss_kind: int = L.LOSS_L1, capacity: int = None, tile=(16, 16), lr: dict = None,
+                 dssim: float = 0.0):
         self.params = params
         self.n, self.sh_deg, self.mode = n, sh_deg, mode
         self.rast = Rasterizer(n, sh_deg, mode, sizes, tile=tile, capacity=capacity)
@@ -57,6 +63,10 @@ class TrainStep:
         self.dL = torch.empty_like(self.target)
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.loss_kind = loss_kind
+        self.dssim = float(dssim)
+        self.ssim = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.loss_ws = (torch.empty(L.i4d_photometric_loss_workspace_size(self.rast.views), dtype=torch.uint8,
+                                    device=dev) if self.dssim > 0 else None)
         self.groups = adam_groups(n, sh_deg, steps, lr)
         self.graph = None
 
@@ -66,7 +76,11 @@ class TrainStep:
         r.project(self.params, self.cams)
         r.bin()
         r.composite()
-        L.i4d_loss(r.img, self.target, self.loss_kind, self.dL, self.loss)
+        if self.dssim > 0:
+            L.i4d_photometric_loss(r.views, r.img, self.target, self.dssim, self.dL, self.loss, self.ssim,
+                                   self.loss_ws)
+        else:
+            L.i4d_loss(r.img, self.target, self.loss_kind, self.dL, self.loss)
         r.backward(self.params, self.cams, self.dL)
         L.i4d_adam_step(self.params, r.grads, self.m, self.v, self.groups, self.step_count)
 
