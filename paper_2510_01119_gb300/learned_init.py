@@ -6,7 +6,7 @@ fitted in minutes): its depth maps are pruned on the GPU (Sec. 3.2), the kept po
 neighbourhood features, and targets are rendered from the matching hidden 4D Gaussian scene.  The
 plain method initialises the temporal scale and rotation by the heuristic of Sec. 4.1 / Sec. 3.3;
 the learned one asks the MLP.  Both use the same spatial scale (mean distance to the 3 nearest
-pruned points) and the same training step (slice/project, bin, render, L1, backward, Adam).
+pruned points) and the same training step (slice/project, bin, render, L1 + D-SSIM loss, backward, Adam).
 """
 from __future__ import annotations
 
@@ -145,7 +145,8 @@ def fit(sc: Scene, params: torch.Tensor, iters: int = None, eval_every: int = No
     cfg = sc.cfg
     iters = cfg.iters if iters is None else iters
     eval_every = cfg.eval_every if eval_every is None else eval_every
-    step = T.TrainStep(params, sc.n, 0, 0, [cfg.view] * cfg.batch, steps=iters, loss_kind=L.LOSS_L1)
+    step = T.TrainStep(params, sc.n, 0, 0, [cfg.view] * cfg.batch, steps=iters, loss_kind=L.LOSS_L1,
+                       dssim=T.DSSIM_LAMBDA)
     ev = Evaluator(sc)
     rng = np.random.default_rng(seed)
     nf = sc.bank.shape[0]
