@@ -284,6 +284,35 @@ I4D_API int32_t i4d_prune_points(const float* depth, const uint8_t* rgb, const u
                          int32_t min_support, int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count,
                          float* xyz, float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status,
                          void* ws, size_t ws_bytes, void* stream);
+/*
+ * i4d_adaptive_voxel -- Eq. 6: S_v = lambda_s * (1/F) sum_i D_i / f_i, D_i the mean depth of frame i
+ * over its pixels with positive depth, f_i = cams[i].fx.  Per-frame depth sums are exact (64-bit
+ * fixed point in 2^-32 units; depths are multiples of 2^-32 from 2^-9 up), the rest is float64 in
+ * frame order, so the result does not depend on the launch.
+ *   depth DEVICE F*H*W float32;  cams DEVICE F cameras;  voxel_out DEVICE 1 float
+ *   ws    DEVICE scratch of i4d_adaptive_voxel_workspace_size(F) bytes
+ * Errors: I4D_ERR_ARG (sizes < 1, NULL pointers, lambda_s <= 0), I4D_ERR_WORKSPACE.
+ */
+I4D_API size_t i4d_adaptive_voxel_workspace_size(int32_t F);
+I4D_API int32_t i4d_adaptive_voxel(const float* depth, int32_t F, int32_t W, int32_t H, const i4d_camera* cams,
+                                   float lambda_s, float* voxel_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * i4d_motion_masks -- the static / dynamic split of Sec. 3.2 ("Motion Probability Estimation"):
+ * each frame's low-resolution motion-probability map (h x w, values in [0, 1]) is upsampled
+ * bilinearly to W x H (source coordinate (x + 0.5) w / W - 0.5 clamped to the map, every step a
+ * float32 operation), binned into 256 bins (bin = min(255, floor(256 p))), and Otsu's threshold t of
+ * the frame's histogram (the bin maximising the between-class variance, first maximum on ties) splits
+ * it: mask = 1 (dynamic) where bin > t.  The result feeds i4d_prune_points' dyn input.
+ *   prob        DEVICE F*h*w float32;  mask DEVICE out F*H*W uint8
+ *   thresholds  DEVICE out F int32 (nullable): the per-frame threshold bins
+ *   ws          DEVICE scratch of i4d_motion_masks_workspace_size(F) bytes
+ * Errors: I4D_ERR_ARG (sizes, NULL pointers), I4D_ERR_WORKSPACE.
+ */
+I4D_API size_t i4d_motion_masks_workspace_size(int32_t F);
+I4D_API int32_t i4d_motion_masks(const float* prob, int32_t F, int32_t w, int32_t h, int32_t W, int32_t H,
+                                 uint8_t* mask, int32_t* thresholds, void* ws, size_t ws_bytes, void* stream);
+
 /* Same pruning on a ready float32 point cloud (xyz n x 3; rgb n x 3 float or NULL; t, dyn or NULL). */
 I4D_API int32_t i4d_prune_points_xyz(const float* xyz, const float* rgb, const float* t, const uint8_t* dyn,
                              int64_t n_points, float voxel_static, float voxel_dynamic, int32_t min_support,

@@ -77,6 +77,10 @@ _SIGS = {
     "i4d_loss": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "i4d_psnr": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "i4d_photometric_loss_workspace_size": (c_sz, [ctypes.POINTER(Views)]),
+    "i4d_adaptive_voxel_workspace_size": (c_sz, [c_i32]),
+    "i4d_adaptive_voxel": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, ctypes.c_float, c_vp, c_vp, c_sz, c_vp]),
+    "i4d_motion_masks_workspace_size": (c_sz, [c_i32]),
+    "i4d_motion_masks": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "i4d_photometric_loss": (c_i32, [ctypes.POINTER(Views), c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_sz,
                                      c_vp]),
     "i4d_adam_step": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(AdamGroup), c_i32, c_vp, c_f, c_f, c_f,
@@ -207,6 +211,28 @@ def i4d_render_bwd(g: Gaussians, views: Views, cams, settings, proj, touched, id
 def i4d_loss(img, target, kind: int, dL_dimg, loss_out, stream=None):
     check(load().i4d_loss(ptr(img), ptr(target), img.numel(), int(kind), ptr(dL_dimg), ptr(loss_out),
                           stream_ptr(stream)), "i4d_loss")
+
+
+def i4d_adaptive_voxel_workspace_size(F: int) -> int:
+    return int(load().i4d_adaptive_voxel_workspace_size(int(F)))
+
+
+def i4d_adaptive_voxel(depth, cams, lambda_s: float, voxel_out, ws, stream=None):
+    """depth: (F, H, W) float32 CUDA tensor; cams: (F, 20) camera tensor; voxel_out: 1 float."""
+    F, H, W = depth.shape
+    check(load().i4d_adaptive_voxel(ptr(depth), int(F), int(W), int(H), ptr(cams), float(lambda_s), ptr(voxel_out),
+                                    ptr(ws), ws.numel() * ws.element_size(), stream_ptr(stream)), "i4d_adaptive_voxel")
+
+
+def i4d_motion_masks_workspace_size(F: int) -> int:
+    return int(load().i4d_motion_masks_workspace_size(int(F)))
+
+
+def i4d_motion_masks(prob, W: int, H: int, mask, thresholds, ws, stream=None):
+    """prob: (F, h, w) float32 CUDA tensor; mask: (F, H, W) uint8; thresholds: (F,) int32 or None."""
+    F, h, w = prob.shape
+    check(load().i4d_motion_masks(ptr(prob), int(F), int(w), int(h), int(W), int(H), ptr(mask), ptr(thresholds),
+                                  ptr(ws), ws.numel() * ws.element_size(), stream_ptr(stream)), "i4d_motion_masks")
 
 
 def i4d_photometric_loss_workspace_size(views: Views) -> int:

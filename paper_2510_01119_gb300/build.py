@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libi4d.so")
 SOURCES = ["api.cu", "slice_project.cu", "binning.cu", "render.cu", "optim.cu", "prune.cu", "init.cu",
            "profile.cu", "render_noalloc.cu",
-           "knn.cu", "mlp.cu", "ssim.cu"]
+           "knn.cu", "mlp.cu", "ssim.cu", "prune_inputs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

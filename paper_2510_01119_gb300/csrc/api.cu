@@ -185,6 +185,25 @@ int32_t i4d_loss(const float* img, const float* target, int64_t count, int32_t k
   return cuda_status(launch_loss(img, target, count, kind, dL_dimg, loss_out, (cudaStream_t)stream));
 }
 
+size_t i4d_adaptive_voxel_workspace_size(int32_t F) { return F > 0 ? adaptive_voxel_workspace_bytes(F) : 0; }
+
+int32_t i4d_adaptive_voxel(const float* depth, int32_t F, int32_t W, int32_t H, const i4d_camera* cams,
+                           float lambda_s, float* voxel_out, void* ws, size_t ws_bytes, void* stream) {
+  if (F < 1 || W < 1 || H < 1 || !depth || !cams || !voxel_out || !ws || !(lambda_s > 0.0f)) return I4D_ERR_ARG;
+  if (ws_bytes < adaptive_voxel_workspace_bytes(F)) return I4D_ERR_WORKSPACE;
+  return cuda_status(launch_adaptive_voxel(depth, F, H, W, cams, lambda_s, voxel_out, ws, (cudaStream_t)stream));
+}
+
+size_t i4d_motion_masks_workspace_size(int32_t F) { return F > 0 ? motion_mask_workspace_bytes(F) : 0; }
+
+int32_t i4d_motion_masks(const float* prob, int32_t F, int32_t w, int32_t h, int32_t W, int32_t H, uint8_t* mask,
+                         int32_t* thresholds, void* ws, size_t ws_bytes, void* stream) {
+  if (F < 1 || w < 1 || h < 1 || W < 1 || H < 1 || (int64_t)W * H >= (1ll << 31) || !prob || !mask || !ws)
+    return I4D_ERR_ARG;
+  if (ws_bytes < motion_mask_workspace_bytes(F)) return I4D_ERR_WORKSPACE;
+  return cuda_status(launch_motion_masks(prob, F, h, w, H, W, mask, thresholds, ws, (cudaStream_t)stream));
+}
+
 size_t i4d_photometric_loss_workspace_size(const i4d_views* views) {
   ViewTable vt;
   if (!make_view_table(views, vt)) return 0;

@@ -44,6 +44,14 @@ cudaError_t launch_loss(const float* img, const float* target, int64_t count, in
                         float* loss_out, cudaStream_t st);
 cudaError_t launch_psnr(const float* img, const float* target, int64_t count, float* psnr_out, cudaStream_t st);
 
+// pruning inputs: adaptive voxel edge (Eq. 6) and Otsu motion masks
+size_t adaptive_voxel_workspace_bytes(int F);
+cudaError_t launch_adaptive_voxel(const float* depth, int F, int H, int W, const i4d_camera* cams, float lambda_s,
+                                  float* out, void* ws, cudaStream_t st);
+size_t motion_mask_workspace_bytes(int F);
+cudaError_t launch_motion_masks(const float* prob, int F, int h, int w, int H, int W, uint8_t* mask, int32_t* thresh,
+                                void* ws, cudaStream_t st);
+
 // (1 - lambda) L1 + lambda (1 - SSIM) over all views, with its gradient
 size_t photometric_workspace_bytes(const ViewTable& vt);
 cudaError_t launch_photometric_loss(const ViewTable& vt, const float* img, const float* target, float lam,

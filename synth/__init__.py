@@ -331,3 +331,17 @@ def depth_video(seed: int = 2, n_frames: int = 200, W: int = 640, H: int = 360, 
         dyn[fi] = (hit_kind >= 10).astype(np.uint8)
     times = np.array([k / max(n_frames - 1, 1) for k in frames], np.float32)
     return dict(depth=depth, rgb=rgb, dyn=dyn, cams=cams, times=times)
+
+
+def motion_prob_maps(dyn: np.ndarray, factor: int = 8, noise: float = 0.12, seed: int = 0) -> np.ndarray:
+    """Low-resolution motion-probability maps (F, ceil(H/factor), ceil(W/factor)) float32 in [0, 1],
+    standing in for the SLAM network's per-frame maps: the fraction of moving pixels in each
+    factor x factor cell of the dynamic mask, plus seeded Gaussian noise, clipped."""
+    dyn = np.asarray(dyn, np.float32)
+    F, H, W = dyn.shape
+    h, w = -(-H // factor), -(-W // factor)
+    pad = np.zeros((F, h * factor, w * factor), np.float32)
+    pad[:, :H, :W] = dyn
+    frac = pad.reshape(F, h, factor, w, factor).mean(axis=(2, 4))
+    r = np.random.default_rng(seed)
+    return np.clip(frac + r.normal(0.0, noise, size=frac.shape), 0.0, 1.0).astype(np.float32)
