@@ -269,7 +269,10 @@ I4D_API int32_t i4d_adam_step(float* params, const float* grads, float* m, float
  * floor(float32(x * (1 / S_v))) per axis, the dynamic flag is part of the key (static and dynamic
  * points never share a voxel, each flag with its own S_v), aggregation in a device hash table
  * (count, sums in 64-bit fixed point, minimum point index), voxels with fewer than min_support
- * points dropped, output ordered by representative (minimum) point index.
+ * points dropped, output ordered by representative (minimum) point index.  voxel_dynamic = 0
+ * leaves the dynamic points unpruned (the Full model of Sec. 4.1): each is kept as its own voxel
+ * whatever min_support (the table then needs a slot per dynamic point).  The Lite model is
+ * voxel_static = voxel_dynamic = 4 units of Eq. 6 (see i4d_adaptive_voxel).
  *   depth    DEVICE F*H*W float32;  rgb: DEVICE F*H*W*3 uint8 or NULL;  dyn: F*H*W uint8 or NULL
  *   cams     DEVICE F cameras (time = frame time)
  *   outputs  DEVICE, capacity entries each: rep (uint32 point index f*H*W + py*W + px),

@@ -203,7 +203,8 @@ def prune(xyz: np.ndarray, voxel_static: float, voxel_dynamic: float = None, min
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
     npts = xyz.shape[0]
     inv_s = np.float32(1.0) / np.float32(voxel_static)
-    inv_d = np.float32(1.0) / np.float32(voxel_dynamic if voxel_dynamic is not None else voxel_static)
+    vd = voxel_dynamic if voxel_dynamic is not None else voxel_static
+    inv_d = np.float32(0.0) if vd == 0 else np.float32(1.0) / np.float32(vd)  # 0: dynamic points unpruned
     cap = max(npts, 1)
     rep = np.zeros(cap, dtype=np.uint32)
     cnt = np.zeros(cap, dtype=np.int32)

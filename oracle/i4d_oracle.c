@@ -942,7 +942,9 @@ static int64_t voxel_coord(float x, float inv) {
 
 /*
  * Grid pruning of a point cloud: key = (dynamic flag, voxel coordinates); the flag makes static
- * and dynamic points never share a voxel, each with its own voxel size.  Points are grouped by
+ * and dynamic points never share a voxel, each with its own voxel size.  inv_dynamic = 0 leaves
+ * the dynamic points unpruned (Sec. 4.1, Full model): each is its own group, kept whatever
+ * min_support.  Points are grouped by
  * key; groups with fewer than min_support points are dropped; each kept voxel reports its point
  * count, the minimum point index (the representative), the centroid and the mean colour and
  * time.  Output is ordered by representative index.  rgb, t, dyn may be NULL (zero / static).
@@ -957,9 +959,15 @@ long orc_prune(long npts, const float* xyz, const float* rgb, const float* t, co
     const int f = dyn ? (dyn[i] != 0) : 0;
     const float inv = f ? inv_dynamic : inv_static;
     keys[i].k[0] = f;
-    keys[i].k[1] = voxel_coord(xyz[3 * i + 0], inv);
-    keys[i].k[2] = voxel_coord(xyz[3 * i + 1], inv);
-    keys[i].k[3] = voxel_coord(xyz[3 * i + 2], inv);
+    if (f && inv_dynamic == 0.0f) {  /* unpruned: a key of its own (no voxel key has k[1] = INT64_MIN) */
+      keys[i].k[1] = INT64_MIN;
+      keys[i].k[2] = i;
+      keys[i].k[3] = 0;
+    } else {
+      keys[i].k[1] = voxel_coord(xyz[3 * i + 0], inv);
+      keys[i].k[2] = voxel_coord(xyz[3 * i + 1], inv);
+      keys[i].k[3] = voxel_coord(xyz[3 * i + 2], inv);
+    }
     keys[i].idx = i;
   }
   qsort(keys, npts, sizeof(pkey), pkey_cmp);
@@ -969,7 +977,7 @@ long orc_prune(long npts, const float* xyz, const float* rgb, const float* t, co
   for (long i = 0; i < npts;) {
     long j = i;
     while (j < npts && memcmp(keys[j].k, keys[i].k, sizeof(keys[i].k)) == 0) ++j;
-    if (j - i >= min_support) {
+    if (j - i >= min_support || (keys[i].k[0] && inv_dynamic == 0.0f)) {
       g[ng].rep = keys[i].idx; /* sorted by idx within the group: first is the minimum */
       g[ng].first = i;
       g[ng].count = j - i;

@@ -327,7 +327,7 @@ static int32_t prune_common(const float* depth, const uint8_t* rgb8, const uint8
                             int64_t table_slots, int64_t capacity, uint32_t* rep, int32_t* count, float* xyz_out,
                             float* rgb_out, float* t_out, uint8_t* flag, int64_t* n_kept, int32_t* status, void* ws,
                             size_t ws_bytes, void* stream) {
-  if (!(voxel_static > 0.0f) || !(voxel_dynamic > 0.0f) || min_support < 1 || capacity < 1 || table_slots < 1 ||
+  if (!(voxel_static > 0.0f) || !(voxel_dynamic >= 0.0f) || min_support < 1 || capacity < 1 || table_slots < 1 ||
       (table_slots & (table_slots - 1)) || table_slots >= (1ll << 32))
     return I4D_ERR_ARG;
   if (!rep || !count || !xyz_out || !rgb_out || !t_out || !flag || !n_kept || !status || !ws) return I4D_ERR_ARG;
@@ -337,7 +337,8 @@ static int32_t prune_common(const float* depth, const uint8_t* rgb8, const uint8
   PruneOut out{rep, count, xyz_out, rgb_out, t_out, flag, n_kept, status};
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
   // the voxel index is floor of x times the float32 reciprocal of the voxel size
-  const float inv_s = 1.0f / voxel_static, inv_d = 1.0f / voxel_dynamic;
+  // voxel_dynamic = 0: dynamic points are not pruned (inv_d = 0 marks it for the kernels)
+  const float inv_s = 1.0f / voxel_static, inv_d = voxel_dynamic > 0.0f ? 1.0f / voxel_dynamic : 0.0f;
   if (e == cudaSuccess)
     e = launch_prune(depth, rgb8, dyn, cams, F, W, H, xyz, rgbf, tpt, n_points, inv_s, inv_d, min_support,
                      table_slots, capacity, out, ws, st);

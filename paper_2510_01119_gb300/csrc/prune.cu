@@ -44,8 +44,9 @@ __device__ __forceinline__ int64_t voxel_coord(float x, float inv) { return (int
 
 __device__ __forceinline__ bool make_key(float x, float y, float z, int flag, float inv, uint64_t& key) {
   const int64_t ix = voxel_coord(x, inv), iy = voxel_coord(y, inv), iz = voxel_coord(z, inv);
-  // (iz stops one short of the top so that no key can equal the all-ones empty marker)
-  if (ix < -kCoordHalf || ix >= kCoordHalf || iy < -kCoordHalf || iy >= kCoordHalf || iz < -kCoordHalf ||
+  // (iz stops one short of the top so that no key can equal the all-ones empty marker; ix too, so
+  // that the x field's top value is free for the keys of unpruned points)
+  if (ix < -kCoordHalf || ix >= kCoordHalf - 1 || iy < -kCoordHalf || iy >= kCoordHalf || iz < -kCoordHalf ||
       iz >= kCoordHalf - 1)
     return false;
   const uint64_t m = (1ull << kCoordBits) - 1;
@@ -53,6 +54,12 @@ __device__ __forceinline__ bool make_key(float x, float y, float z, int flag, fl
         ((uint64_t)(iz + kCoordHalf) & m);
   return true;
 }
+
+// A dynamic point that is not pruned (voxel_dynamic = 0, the Full model of Sec. 4.1) forms a voxel
+// of its own: dynamic flag, the x field's top value (no voxel key has it) and its index.
+constexpr uint64_t kUnprunedTag = (1ull << 22) - 1;  // flag bit + 21 ones, in bits 42..63
+__device__ __forceinline__ uint64_t unpruned_key(uint32_t idx) { return (kUnprunedTag << 42) | (uint64_t)idx; }
+__device__ __forceinline__ bool is_unpruned(uint64_t key) { return (key >> 42) == kUnprunedTag; }
 
 __device__ __forceinline__ unsigned long long to_fix(float x) {
   return (unsigned long long)(long long)llrint((double)x * kFix);
@@ -140,8 +147,13 @@ __global__ void __launch_bounds__(256) insert_depth_kernel(const float* __restri
     const float y = c.R[1] * dx + c.R[4] * dy + c.R[7] * dz;
     const float z = c.R[2] * dx + c.R[5] * dy + c.R[8] * dz;
     const int flag = dyn ? (dyn[pi] != 0) : 0;
-    valid = make_key(x, y, z, flag, flag ? inv_d : inv_s, key);
-    if (!valid) set_status(status, I4D_ERR_CAPACITY);
+    if (flag && inv_d == 0.0f) {
+      key = unpruned_key(idx);
+      valid = true;
+    } else {
+      valid = make_key(x, y, z, flag, flag ? inv_d : inv_s, key);
+      if (!valid) set_status(status, I4D_ERR_CAPACITY);
+    }
     s[0] = to_fix(x);
     s[1] = to_fix(y);
     s[2] = to_fix(z);
@@ -166,8 +178,13 @@ __global__ void __launch_bounds__(256) insert_xyz_kernel(const float* __restrict
   if (i < n) {
     const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     const int flag = dyn ? (dyn[i] != 0) : 0;
-    valid = make_key(x, y, z, flag, flag ? inv_d : inv_s, key);
-    if (!valid) set_status(status, I4D_ERR_CAPACITY);
+    if (flag && inv_d == 0.0f) {
+      key = unpruned_key((uint32_t)i);
+      valid = true;
+    } else {
+      valid = make_key(x, y, z, flag, flag ? inv_d : inv_s, key);
+      if (!valid) set_status(status, I4D_ERR_CAPACITY);
+    }
     s[0] = to_fix(x);
     s[1] = to_fix(y);
     s[2] = to_fix(z);
@@ -184,7 +201,8 @@ __global__ void __launch_bounds__(256) insert_xyz_kernel(const float* __restrict
 __global__ void table_flags_kernel(Table T, int min_support, uint32_t* __restrict__ flags) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= T.slots) return;
-  flags[s] = (T.keys[s] != kEmpty && T.cnt[s] >= (uint32_t)min_support) ? 1u : 0u;
+  const uint64_t k = T.keys[s];
+  flags[s] = (k != kEmpty && (T.cnt[s] >= (uint32_t)min_support || is_unpruned(k))) ? 1u : 0u;
 }
 
 __global__ void table_compact_kernel(Table T, const uint32_t* __restrict__ flags, const uint32_t* __restrict__ offs,

@@ -63,3 +63,32 @@ class Pruner:
         k = int(o["n_kept"].item())
         return {key: (v[:k].cpu().numpy() if key not in ("n_kept", "status") else v.cpu().numpy())
                 for key, v in o.items()}
+
+
+def adaptive_voxel(depth: torch.Tensor, cams: torch.Tensor, lambda_s: float = 1.0) -> torch.Tensor:
+    """Eq. 6 on the GPU: lambda_s times the mean over frames of mean depth / focal length (1 float)."""
+    out = torch.zeros(1, dtype=torch.float32, device=depth.device)
+    ws = torch.empty(L.i4d_adaptive_voxel_workspace_size(depth.shape[0]), dtype=torch.uint8, device=depth.device)
+    L.i4d_adaptive_voxel(depth, cams, lambda_s, out, ws)
+    return out
+
+
+def motion_masks(prob: torch.Tensor, W: int, H: int):
+    """Otsu masks of the low-resolution motion-probability maps (F, h, w) at W x H: (masks, thresholds)."""
+    F = prob.shape[0]
+    mask = torch.empty(F, H, W, dtype=torch.uint8, device=prob.device)
+    th = torch.empty(F, dtype=torch.int32, device=prob.device)
+    ws = torch.empty(L.i4d_motion_masks_workspace_size(F), dtype=torch.uint8, device=prob.device)
+    L.i4d_motion_masks(prob, W, H, mask, th, ws)
+    return mask, th
+
+
+def model_voxels(model: str, unit: float):
+    """(voxel_static, voxel_dynamic) of the paper's two models (Sec. 4.1) for the Eq. 6 unit
+    (lambda_s = 1): Lite prunes both regions at 4 units; Full prunes static regions at 1 unit and
+    keeps every dynamic point (voxel_dynamic = 0)."""
+    if model == "lite":
+        return 4.0 * unit, 4.0 * unit
+    if model == "full":
+        return 1.0 * unit, 0.0
+    raise ValueError(model)

@@ -117,6 +117,28 @@ def test_prune_xyz_kept_set_bit_exact(dev, orc, min_support):
     assert np.allclose(got["t"], want["t"], atol=1e-6)
 
 
+@pytest.mark.parametrize("variant", ["full", "lite"])
+def test_prune_variants_bit_exact(dev, orc, variant):
+    """The Full model (dynamic points unpruned, voxel_dynamic = 0) and the Lite model (one coarse
+    voxel for both flags): kept set, counts and flags bit-exact, centroids to float rounding."""
+    r = np.random.default_rng(60)
+    n = 150000
+    xyz = (r.normal(size=(n, 3)) * 0.4).astype(np.float32)
+    rgb = r.uniform(size=(n, 3)).astype(np.float32)
+    t = r.uniform(size=n).astype(np.float32)
+    dyn = (r.uniform(size=n) < 0.2).astype(np.uint8)
+    vs, vd, k = (0.01, 0.0, 3) if variant == "full" else (0.04, 0.04, 2)
+    got = _prune_gpu(xyz, rgb, t, dyn, vs, vd, k, slots=1 << 18)
+    want = orc.prune(xyz, vs, vd, k, rgb=rgb, t=t, dyn=dyn)
+    assert np.array_equal(got["rep"].astype(np.int64), want["rep"].astype(np.int64))
+    assert np.array_equal(got["count"], want["count"])
+    assert np.array_equal(got["flag"], want["flag"])
+    assert np.allclose(got["xyz"], want["centroid"], rtol=1e-6, atol=1e-7)
+    assert np.allclose(got["t"], want["t"], atol=1e-6)
+    if variant == "full":
+        assert int(got["flag"].sum()) == int(dyn.sum())
+
+
 def test_prune_depth_video_matches_oracle(dev, orc):
     """Depth maps -> fused back-projection + pruning.  The GPU back-projects in FP32, the oracle in
     FP64: points whose voxel coordinate sits within 1e-4 voxels of a cell boundary may land in the

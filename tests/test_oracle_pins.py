@@ -496,6 +496,31 @@ def test_prune_matches_numpy_groupby(orc, min_support):
     assert np.all(out["centroid"] >= cells * vsz - 1e-6) and np.all(out["centroid"] <= (cells + 1) * vsz + 1e-6)
 
 
+def test_prune_full_variant_keeps_every_dynamic_point(orc):
+    """voxel_dynamic = 0 (the Full model): static points are pruned as usual, and every dynamic point
+    is kept as its own voxel, whatever the minimum support."""
+    r = np.random.default_rng(40)
+    n = 8000
+    xyz = (r.normal(size=(n, 3)) * 0.2).astype(np.float32)
+    t = r.uniform(0, 1, n).astype(np.float32)
+    dyn = (r.uniform(size=n) < 0.25).astype(np.uint8)
+    vs, ms = 0.05, 3
+    out = orc.prune(xyz, vs, 0.0, ms, t=t, dyn=dyn)
+    # static part: numpy group-by with the minimum support
+    st = np.nonzero(dyn == 0)[0]
+    cell = np.floor(xyz[st] * (np.float32(1) / np.float32(vs))).astype(np.int64)
+    uk, inverse, counts = np.unique(cell, axis=0, return_inverse=True, return_counts=True)
+    rep = np.full(len(uk), n, np.int64)
+    np.minimum.at(rep, inverse.reshape(-1), st)
+    want_rep = np.sort(np.concatenate([rep[counts >= ms], np.nonzero(dyn)[0]]))
+    assert np.array_equal(out["rep"], want_rep)
+    d = dyn[out["rep"]] == 1
+    assert np.array_equal(out["flag"], dyn[out["rep"]])
+    assert np.all(out["count"][d] == 1)
+    assert np.array_equal(out["centroid"][d], xyz[out["rep"][d]].astype(np.float64))
+    assert np.array_equal(out["t"][d], t[out["rep"][d]].astype(np.float64))
+
+
 # ---------------------------------------------------------------------------------------------
 # Adam
 # ---------------------------------------------------------------------------------------------
