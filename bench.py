@@ -349,7 +349,52 @@ def _time_oracle(g, cam, n_pix, threads):
     return time.perf_counter() - t0
 
 
-def run_configs(dev, wl):
+def _time_call(fn, reps=10):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def prune_inputs_and_models(dev, vid):
+    """The pruning inputs of Sec. 3.2 (Eq. 6 voxel edge, Otsu motion masks from synthetic motion
+    maps) and the Lite / Full pruning of the 200-frame video, timed on the GPU."""
+    import torch
+
+    import synth
+    from paper_2510_01119_gb300 import prune as PR
+    from paper_2510_01119_gb300 import rasterizer as R
+    depth = torch.from_numpy(vid["depth"]).to(dev)
+    rgb = torch.from_numpy(vid["rgb"]).to(dev)
+    cams = R.cameras_tensor(vid["cams"], dev)
+    F, H, W = vid["depth"].shape
+    prob = torch.from_numpy(synth.motion_prob_maps(vid["dyn"], 8, seed=4)).to(dev)
+    out = {"adaptive_voxel_ms": _time_call(lambda: PR.adaptive_voxel(depth, cams, 1.0)),
+           "motion_masks_ms": _time_call(lambda: PR.motion_masks(prob, W, H))}
+    unit = float(PR.adaptive_voxel(depth, cams, 1.0).item())
+    masks, _ = PR.motion_masks(prob, W, H)
+    out["voxel_unit"] = unit
+    out["otsu_dynamic_fraction"] = float(masks.float().mean().item())
+    for model in ("lite", "full"):
+        vs, vd = PR.model_voxels(model, unit)
+        pr = PR.Pruner(F * W * H, 1 << 26, capacity=1 << 25, device=dev)
+        ms = _time_call(lambda: pr.prune_depth(depth, rgb, masks, cams, vs, vd, 3), reps=3)
+        if int(pr.out["status"].item()) != 0:
+            raise RuntimeError("pruning overflowed its table")
+        out[model] = {"voxel_static": vs, "voxel_dynamic": vd, "prune_ms": ms,
+                      "n_kept": int(pr.out["n_kept"].item())}
+        del pr
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_configs(dev, wl, vid):
     import torch
 
     import oracle
@@ -381,6 +426,7 @@ def run_configs(dev, wl):
     cams = R.cameras_tensor([synth.arc_camera(int(f), N_FRAMES, W, H) for f, (W, H) in zip(frames, sizes)], dev)
     ms, inst = _time_render(wl["params"], wl["n"], 0, cams, sizes, dev)
     out["render_1M_16views"] = {"gpu_ms_fwd_bwd": ms, "instances": inst, "prune_ms": wl["prune_ms"]}
+    out["prune_inputs_and_models"] = prune_inputs_and_models(dev, vid)
     oracle.set_threads(nthr)
     return out
 
@@ -643,7 +689,7 @@ def run_ours(args, ws, rank, local):
     if args.small:
         line["config"]["workload"] = "train_step_small_profile_only"
     if args.configs and rank == 0:
-        line["configs"] = run_configs(dev, wl)
+        line["configs"] = run_configs(dev, wl, vid)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.small:
         import oracle
         oracle.build()
