@@ -67,6 +67,24 @@ def test_argument_errors_are_reported_not_launched(lib):
     assert rc == -1
     assert lib.i4d_adam_step(None, None, None, None, 6, None, 0, None, 0.9, 0.999, 1e-15, None) == -1
     assert lib.i4d_loss(None, None, 10, 5, None, None, None) == -1
+    # photometric loss: lambda outside [0, 1]; workspace too small
+    fake = ctypes.c_void_p(16)
+    assert lib.i4d_photometric_loss(ctypes.byref(ok), fake, fake, ctypes.c_float(1.5), fake, fake, None, fake,
+                                    1 << 30, None) == -1
+    assert lib.i4d_photometric_loss(ctypes.byref(ok), fake, fake, ctypes.c_float(0.2), fake, fake, None, fake,
+                                    8, None) == -4
+    assert L.i4d_photometric_loss_workspace_size(ok) >= 9 * 4 * 128 * 96
+    # pruning inputs: no frames, non-positive lambda; a negative dynamic voxel edge
+    assert lib.i4d_adaptive_voxel(fake, 0, 4, 4, fake, ctypes.c_float(1.0), fake, fake, 1 << 20, None) == -1
+    assert lib.i4d_adaptive_voxel(fake, 2, 4, 4, fake, ctypes.c_float(0.0), fake, fake, 1 << 20, None) == -1
+    assert lib.i4d_motion_masks(fake, 0, 4, 4, 8, 8, fake, None, fake, 1 << 20, None) == -1
+    assert lib.i4d_motion_masks(fake, 2, 4, 4, 8, 8, fake, None, fake, 4, None) == -4
+    assert L.i4d_motion_masks_workspace_size(3) >= 3 * 1024 and L.i4d_adaptive_voxel_workspace_size(3) >= 36
+    # voxel_dynamic may be 0 (dynamic points unpruned) but not negative
+    args = lambda vd: (fake, None, None, None, 100, ctypes.c_float(0.01), ctypes.c_float(vd), 1, 1 << 10, 100,
+                       fake, fake, fake, fake, fake, fake, fake, fake, fake, 8, None)
+    assert lib.i4d_prune_points_xyz(*args(-0.01)) == -1
+    assert lib.i4d_prune_points_xyz(*args(0.0)) == -4            # accepted, then the workspace is too small
 
 
 def test_no_cpu_fallback_without_library(tmp_path):
