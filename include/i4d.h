@@ -98,7 +98,16 @@ typedef struct {
   int32_t sh_deg;       /* 0..3 */
   int32_t mode;         /* I4D_MODE_* (Sec. 3.3 "Isotropic Gaussian": ISO modes tie s_x = s_y = s_z
                            to logscale.x; ISO_IDENTITY also fixes R = I) */
+  int32_t sch_terms;    /* 0 or 1: the colour of the method (base RGB + SH).  N_t in 2..I4D_MAX_SCH_TERMS:
+                           the SCH appearance of the 4DGS it compares against (Sec. 3.1, Table 2 "SCH"):
+                           colour += sum_{m=1}^{N_t-1} cos(2 pi m t) (c_m0 + sum_{k>=1} Y_k c_mk), t the
+                           view's frame time (period = the normalised video length 1), Y_k the real SH of
+                           the Gaussians' SH degree; the (N_t - 1)(deg + 1)^2 x 3 coefficients follow the
+                           SH planes, coefficient (m, k, ch) at float (m - 1)(deg + 1)^2 3 + 3 k + ch of the
+                           Gaussian's SCH block (plane = float / 4, lane = float % 4) */
 } i4d_gaussians;
+
+#define I4D_MAX_SCH_TERMS 8
 
 /* Thresholds of the renderer (host).  The paper leaves them to the 3D splatting renderer it
  * builds on; i4d_default_settings() gives alpha_max 0.99, alpha_min 1/255, T_min 1e-4,
@@ -134,6 +143,8 @@ I4D_API const char* i4d_status_string(int32_t status);
 I4D_API void i4d_default_settings(i4d_settings* out /* host */);
 /* Floats per Gaussian in the flat parameter layout: 20 + 4 K. */
 I4D_API int64_t i4d_param_floats(int32_t sh_deg);
+/* The same with the SCH variant's coefficients (sch_terms as in i4d_gaussians). */
+I4D_API int64_t i4d_param_floats_sch(int32_t sh_deg, int32_t sch_terms);
 
 /*
  * i4d_slice_project -- Eq. 7-8 (conditional mean mu_xyz|t and covariance Sigma_xyz|t of each 4D

@@ -109,14 +109,23 @@ def _gauss_arrays(g: dict):
             _f64(g["ql"]), _f64(g["qr"]), _f64(g["opacity"]), _f64(g["rgb"]), np.ascontiguousarray(sh_arr))
 
 
+def _sch_arrays(g: dict):
+    """SCH variant (sch_terms N_t > 1): (N_t, coefficients (n, N_t - 1, (deg + 1)^2, 3) as float64 or None)."""
+    nt = int(g.get("sch_terms", 0))
+    if nt <= 1:
+        return 0, None
+    return nt, _f64(np.asarray(g["sch"]).reshape(g["mean4"].shape[0], nt - 1, (int(g.get("sh_deg", 0)) + 1) ** 2, 3))
+
+
 def project(g: dict, cam: dict, tile=(16, 16), settings=None) -> np.ndarray:
     """Eq. 7-8 slicing, temporal opacity, EWA projection and colour for every Gaussian -> (n, 27)."""
     lib = _load()
     n, deg, mode, m4, ls4, ql, qr, op, rgb, sh = _gauss_arrays(g)
     S = settings if settings is not None else settings_array()
     out = np.zeros((n, len(PCOLS)), dtype=np.float64)
+    nt, sch = _sch_arrays(g)
     rc = lib.orc_project(n, deg, mode, _ptr(m4), _ptr(ls4), _ptr(ql), _ptr(qr), _ptr(op), _ptr(rgb), _ptr(sh),
-                         _ptr(camera_array(cam)), int(tile[0]), int(tile[1]), _ptr(S), _ptr(out))
+                         nt, _ptr(sch), _ptr(camera_array(cam)), int(tile[0]), int(tile[1]), _ptr(S), _ptr(out))
     if rc != 0:
         raise ValueError(f"orc_project failed ({rc})")
     return out
@@ -159,10 +168,14 @@ def render_bwd(g: dict, cam: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), sett
     g2 = np.zeros((n, 9), dtype=np.float64)
     grads = dict(mean4=np.zeros((n, 4)), logscale4=np.zeros((n, 4)), ql=np.zeros((n, 4)), qr=np.zeros((n, 4)),
                  opacity=np.zeros(n), rgb=np.zeros((n, 3)), sh=np.zeros((n, 15, 3)))
+    nt, sch = _sch_arrays(g)
+    if nt > 1:
+        grads["sch"] = np.zeros_like(sch)
     rc = lib.orc_render_bwd(n, deg, mode, _ptr(m4), _ptr(ls4), _ptr(ql), _ptr(qr), _ptr(op), _ptr(rgb), _ptr(sh),
-                            _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), _ptr(gimg),
+                            nt, _ptr(sch), _ptr(camera_array(cam)), _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), _ptr(gimg),
                             _ptr(g2), _ptr(grads["mean4"]), _ptr(grads["logscale4"]), _ptr(grads["ql"]),
-                            _ptr(grads["qr"]), _ptr(grads["opacity"]), _ptr(grads["rgb"]), _ptr(grads["sh"]))
+                            _ptr(grads["qr"]), _ptr(grads["opacity"]), _ptr(grads["rgb"]), _ptr(grads["sh"]),
+                            _ptr(grads.get("sch")))
     if rc != 0:
         raise RuntimeError(f"orc_render_bwd failed ({rc})")
     grads["sh"] = grads["sh"][:, : (deg + 1) ** 2 - 1, :]

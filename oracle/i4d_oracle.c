@@ -182,9 +182,19 @@ static double frac_margin(double x) {
   return f < 1.0 - f ? f : 1.0 - f;
 }
 
+/*
+ * SCH variant (Sec. 3.1, the 4DGS appearance model): nt temporal terms; for m = 1..nt-1 the colour
+ * gains cos(2 pi m t) (c_m0 + sum_k Y_k c_mk) with t the camera's frame time.  Coefficient
+ * (m, k, ch), k = 0 the constant harmonic, sits at ((m - 1)(K + 1) + k) 3 + ch of the Gaussian's
+ * block of sch_stride(deg, nt) doubles.
+ */
+static const double kPi = 3.14159265358979323846;
+
+static int sch_stride(int deg, int nt) { return nt > 1 ? (nt - 1) * (deg + 1) * (deg + 1) * 3 : 0; }
+
 static void forward_one(int i, int sh_deg, int mode, const double* mean4, const double* logscale4,
                         const double* ql, const double* qr, const double* opac, const double* rgb,
-                        const double* sh, const double* cam, int tile_w, int tile_h,
+                        const double* sh, int nt, const double* sch, const double* cam, int tile_w, int tile_h,
                         const double* S, gfwd* f) {
   memset(f, 0, sizeof(*f));
   const double* mu = mean4 + 4 * i;
@@ -319,6 +329,13 @@ static void forward_one(int i, int sh_deg, int mode, const double* mean4, const 
     for (int ch = 0; ch < 3; ++ch) {
       double acc = rgb[3 * i + ch];
       for (int k = 0; k < K; ++k) acc += f->Y[k] * sh[(size_t)i * 45 + 3 * k + ch];
+      for (int m = 1; m < nt; ++m) {
+        const double cs = cos(2.0 * kPi * m * cam[C_TIME]);
+        for (int k = 0; k <= K; ++k) {
+          const double Yk = k == 0 ? 1.0 : f->Y[k - 1];
+          acc += cs * Yk * sch[(size_t)i * sch_stride(sh_deg, nt) + ((size_t)(m - 1) * (K + 1) + k) * 3 + ch];
+        }
+      }
       f->raw[ch] = acc;
       f->rgb[ch] = acc > 0.0 ? acc : 0.0;
     }
@@ -378,13 +395,14 @@ static void store_record(const gfwd* f, double* rec) {
  */
 int orc_project(int n, int sh_deg, int mode, const double* mean4, const double* logscale4,
                 const double* ql, const double* qr, const double* opac, const double* rgb,
-                const double* sh, const double* cam, int tile_w, int tile_h, const double* S,
-                double* out) {
+                const double* sh, int nt, const double* sch, const double* cam, int tile_w, int tile_h,
+                const double* S, double* out) {
   if (n < 0 || sh_deg < 0 || sh_deg > 3 || mode < 0 || mode > 2 || tile_w <= 0 || tile_h <= 0) return -1;
+  if (nt > 1 && !sch) return -1;
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     gfwd f;
-    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, cam, tile_w, tile_h, S, &f);
+    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, tile_w, tile_h, S, &f);
     store_record(&f, out + (size_t)i * P_STRIDE);
   }
   return 0;
@@ -613,9 +631,10 @@ static void pixel_backward(const double* P, const frag* buf, int nblend, double 
  * Chain the 2D gradients of one Gaussian through projection, slicing and the 4D
  * parameterisation to the parameter gradients (accumulated into the g_* arrays).
  */
-static void chain_to_params(int i, int sh_deg, int mode, const double* sh, const double* cam, const gfwd* f,
-                            const double* g2, double* g_mean4, double* g_logscale4, double* g_ql, double* g_qr,
-                            double* g_opac, double* g_rgb, double* g_sh) {
+static void chain_to_params(int i, int sh_deg, int mode, const double* sh, int nt, const double* sch,
+                            const double* cam, const gfwd* f, const double* g2, double* g_mean4,
+                            double* g_logscale4, double* g_ql, double* g_qr, double* g_opac, double* g_rgb,
+                            double* g_sh, double* g_sch) {
   const double fx = cam[C_FX], fy = cam[C_FY];
   const double mz = f->m[2], mx = f->m[0], my = f->m[1];
   double gm[3] = {0, 0, 0};
@@ -691,6 +710,15 @@ static void chain_to_params(int i, int sh_deg, int mode, const double* sh, const
         g_sh[(size_t)i * 45 + 3 * k + ch] += f->Y[k] * grgb[ch];
         const double c = sh[(size_t)i * 45 + 3 * k + ch] * grgb[ch];
         for (int a = 0; a < 3; ++a) gdhat[a] += c * f->dY[k][a];
+      }
+      for (int m = 1; m < nt; ++m) {  /* SCH: d/dc_mk = cos(2 pi m t) Y_k; Y_k (k >= 1) depends on dhat */
+        const double cs = cos(2.0 * kPi * m * cam[C_TIME]);
+        for (int k = 0; k <= K; ++k) {
+          const size_t o = (size_t)i * sch_stride(sh_deg, nt) + ((size_t)(m - 1) * (K + 1) + k) * 3 + ch;
+          g_sch[o] += cs * (k == 0 ? 1.0 : f->Y[k - 1]) * grgb[ch];
+          if (k > 0)
+            for (int a = 0; a < 3; ++a) gdhat[a] += cs * sch[o] * grgb[ch] * f->dY[k - 1][a];
+        }
       }
     }
     const double dd = f->dhat[0] * gdhat[0] + f->dhat[1] * gdhat[1] + f->dhat[2] * gdhat[2];
@@ -780,15 +808,18 @@ static void chain_to_params(int i, int sh_deg, int mode, const double* sh, const
  * (accumulated into g_mean4 .. g_sh, so that several views can be summed by repeated calls).
  */
 int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const double* logscale4, const double* ql,
-                   const double* qr, const double* opac, const double* rgb, const double* sh, const double* cam,
-                   const double* bg, const double* S, int npix, const int* pix, const double* dL_dimg,
-                   double* grad2d, double* g_mean4, double* g_logscale4, double* g_ql, double* g_qr,
-                   double* g_opac, double* g_rgb, double* g_sh) {
+                   const double* qr, const double* opac, const double* rgb, const double* sh, int nt,
+                   const double* sch, const double* cam, const double* bg, const double* S, int npix,
+                   const int* pix, const double* dL_dimg, double* grad2d, double* g_mean4, double* g_logscale4,
+                   double* g_ql, double* g_qr, double* g_opac, double* g_rgb, double* g_sh, double* g_sch) {
   const int W = (int)cam[C_W], H = (int)cam[C_H];
   if (pix == NULL && npix != W * H) return -1;
   double* P = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * P_STRIDE);
   if (!P) return -2;
-  orc_project(n, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, cam, 16, 16, S, P);
+  if (orc_project(n, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, 16, 16, S, P) != 0) {
+    free(P);
+    return -1;
+  }
   memset(grad2d, 0, sizeof(double) * (size_t)n * G_STRIDE);
   int nthreads = orc_max_threads();
   double* part = (double*)calloc((size_t)nthreads * n * G_STRIDE + 1, sizeof(double));
@@ -833,8 +864,9 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
     for (int k = 0; k < G_STRIDE; ++k) any |= (g2[k] != 0.0);
     if (!any) continue;
     gfwd f;
-    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, cam, 16, 16, S, &f);
-    chain_to_params(i, sh_deg, mode, sh, cam, &f, g2, g_mean4, g_logscale4, g_ql, g_qr, g_opac, g_rgb, g_sh);
+    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, 16, 16, S, &f);
+    chain_to_params(i, sh_deg, mode, sh, nt, sch, cam, &f, g2, g_mean4, g_logscale4, g_ql, g_qr, g_opac, g_rgb,
+                    g_sh, g_sch);
   }
   free(P);
   return err;
@@ -1015,7 +1047,7 @@ void orc_cov4(int mode, const double* logscale4, const double* ql, const double*
   const double cam[C_COUNT] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 5, 1, 1, 0, 0, 1, 1, 0};
   const double S[S_COUNT] = {0.99, 1.0 / 255.0, 1e-4, 9.0, 1.0 / 255.0, 0.2, 0.3, 1.3};
   gfwd f;
-  forward_one(0, 0, mode, mean4, logscale4, ql, qr, &opac, rgb, sh, cam, 16, 16, S, &f);
+  forward_one(0, 0, mode, mean4, logscale4, ql, qr, &opac, rgb, sh, 0, NULL, cam, 16, 16, S, &f);
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) Sigma[4 * a + b] = f.Sig[a][b];
 }

@@ -35,7 +35,7 @@ class Views(ctypes.Structure):
 
 
 class Gaussians(ctypes.Structure):
-    _fields_ = [("params", c_vp), ("n", c_i32), ("sh_deg", c_i32), ("mode", c_i32)]
+    _fields_ = [("params", c_vp), ("n", c_i32), ("sh_deg", c_i32), ("mode", c_i32), ("sch_terms", c_i32)]
 
 
 class Settings(ctypes.Structure):
@@ -63,6 +63,7 @@ _SIGS = {
     "i4d_status_string": (ctypes.c_char_p, [c_i32]),
     "i4d_default_settings": (None, [ctypes.POINTER(Settings)]),
     "i4d_param_floats": (c_i64, [c_i32]),
+    "i4d_param_floats_sch": (c_i64, [c_i32, c_i32]),
     "i4d_total_tiles": (c_i64, [ctypes.POINTER(Views)]),
     "i4d_total_pixels": (c_i64, [ctypes.POINTER(Views)]),
     "i4d_slice_project": (c_i32, [ctypes.POINTER(Gaussians), ctypes.POINTER(Views), c_vp, ctypes.POINTER(Settings),

@@ -103,6 +103,11 @@ void i4d_default_settings(i4d_settings* out) {
   out->pad = 0.0f;
 }
 
+int64_t i4d_param_floats_sch(int32_t sh_deg, int32_t sch_terms) {
+  if (sh_deg < 0 || sh_deg > 3 || sch_terms < 0 || sch_terms > I4D_MAX_SCH_TERMS) return -1;
+  return 20 + 4 * sh_planes(sh_deg) + 4 * sch_planes(sh_deg, sch_terms);
+}
+
 int64_t i4d_param_floats(int32_t sh_deg) {
   if (sh_deg < 0 || sh_deg > 3) return -1;
   return 20 + 4 * sh_planes(sh_deg);
@@ -127,8 +132,9 @@ int32_t i4d_slice_project(const i4d_gaussians* g, const i4d_views* views, const 
   if (!make_view_table(views, vt)) return I4D_ERR_ARG;
   if (g->n == 0) return I4D_OK;
   if (!g->params || !cams || !proj || !touched || !aligned16(g->params) || !aligned16(proj)) return I4D_ERR_ARG;
+  if (g->sch_terms < 0 || g->sch_terms > I4D_MAX_SCH_TERMS) return I4D_ERR_ARG;
   return cuda_status(launch_slice_project(g->params, g->n, g->sh_deg, g->mode, vt, cams, to_settings(settings), proj,
-                                          touched, (cudaStream_t)stream));
+                                          touched, (cudaStream_t)stream, g->sch_terms));
 }
 
 size_t i4d_bin_tiles_workspace_size(const i4d_views* views, int32_t n, int64_t capacity) {
@@ -165,6 +171,7 @@ int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, const i4d
                        const float* dL_dimg, float* grad2d, float* grads, void* stream) {
   ViewTable vt;
   if (!g || g->n < 0 || g->sh_deg < 0 || g->sh_deg > 3 || g->mode < 0 || g->mode > 2) return I4D_ERR_ARG;
+  if (g->sch_terms < 0 || g->sch_terms > I4D_MAX_SCH_TERMS) return I4D_ERR_ARG;
   if (!make_view_table(views, vt)) return I4D_ERR_ARG;
   if (g->n == 0) return I4D_OK;
   if (!g->params || !cams || !proj || !touched || !ids || !ranges || !T_final || !last || !dL_dimg || !grad2d ||
@@ -174,7 +181,8 @@ int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, const i4d
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = launch_render_bwd(vt, g->n, proj, ids, ranges, S, T_final, last, dL_dimg, grad2d, st);
   if (e == cudaSuccess)
-    e = launch_slice_project_bwd(g->params, g->n, g->sh_deg, g->mode, vt, cams, S, touched, grad2d, grads, st);
+    e = launch_slice_project_bwd(g->params, g->n, g->sh_deg, g->mode, vt, cams, S, touched, grad2d, grads, st,
+                                 g->sch_terms);
   return cuda_status(e);
 }
 

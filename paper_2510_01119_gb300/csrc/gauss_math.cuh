@@ -195,9 +195,17 @@ I4D_HD int s3(int i, int j) {
   return a == 0 ? b : (a == 1 ? 2 + b : 5);
 }
 
+// Coefficient c of the SCH variant's term m (1..nt-1), harmonic k (0 = the constant, 1.. = the SH
+// basis of degree >= 1), channel ch: float (m - 1)((DEG + 1)^2) 3 + 3 k + ch of the Gaussian's SCH
+// block, which follows its SH planes (plane = float / 4, lane = float % 4).
+template <int DEG>
+I4D_D int sch_index(int m, int k, int ch) {
+  return ((m - 1) * (DEG + 1) * (DEG + 1) + k) * 3 + ch;
+}
+
 template <int DEG>
 I4D_D void view_forward(const GaussState& G, const float4* __restrict__ sh, int n, int gi, const Cam& C,
-                        const float* campos, float tanx, float tany, const Settings& S, ViewFwd& F) {
+                        const float* campos, float tanx, float tany, const Settings& S, ViewFwd& F, int nt = 0) {
   F.dt = C.time - G.mu[3];
   const float inv_c = 1.0f / G.c;
   F.k = F.dt * inv_c;
@@ -289,6 +297,23 @@ I4D_D void view_forward(const GaussState& G, const float4* __restrict__ sh, int 
       F.raw[2] += Y[k] * c[3 * k + 2];
     }
   }
+  if (nt > 1) {
+    // SCH variant (Sec. 3.1): + sum_m cos(2 pi m t) (c_m0 + sum_k Y_k c_mk), t the view's frame time
+    float Y1[16];
+    Y1[0] = 1.0f;
+    if constexpr (DEG > 0) sh_basis<DEG>(F.dhat[0], F.dhat[1], F.dhat[2], Y1 + 1);
+    const float* sch = reinterpret_cast<const float*>(sh + (size_t)sh_planes(DEG) * n);
+    for (int m = 1; m < nt; ++m) {
+      const float cs = cospif(2.0f * (float)m * C.time);
+#pragma unroll
+      for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const int idx = sch_index<DEG>(m, k, ch);
+          F.raw[ch] += cs * Y1[k] * __ldg(&sch[((size_t)(idx >> 2) * n + gi) * 4 + (idx & 3)]);
+        }
+    }
+  }
 }
 
 // ---- per-view reverse mode -----------------------------------------------------------------------------
@@ -301,7 +326,7 @@ struct ParamGrad {
 template <int DEG>
 I4D_D void view_backward(const GaussState& G, const ViewFwd& F, const float4* __restrict__ sh, int n, int gi,
                          const Cam& C, const float* g, ParamGrad& P, float* gsh, float* gA_acc,
-                         float& gc_acc, float* gb_acc) {
+                         float& gc_acc, float* gb_acc, int nt = 0, float4* gsch = nullptr) {
   const float fx = C.fx, fy = C.fy;
   const float mz = F.m[2], imz = 1.0f / mz, imz2 = imz * imz;
   float gm[3] = {0.0f, 0.0f, 0.0f};
@@ -392,6 +417,19 @@ I4D_D void view_backward(const GaussState& G, const ViewFwd& F, const float4* __
         gsh[3 * k + 2] += Y[k] * graw[2];
         w[k] = c[3 * k] * graw[0] + c[3 * k + 1] * graw[1] + c[3 * k + 2] * graw[2];
       }
+      if (nt > 1) {  // the SCH terms' harmonics also depend on the view direction
+        const float* sch = reinterpret_cast<const float*>(sh + (size_t)NP * n);
+        for (int m = 1; m < nt; ++m) {
+          const float cs = cospif(2.0f * (float)m * C.time);
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+              const int idx = sch_index<DEG>(m, k + 1, ch);
+              w[k] += cs * __ldg(&sch[((size_t)(idx >> 2) * n + gi) * 4 + (idx & 3)]) * graw[ch];
+            }
+        }
+      }
       float gx, gy, gz;
       sh_basis_grad<DEG>(F.dhat[0], F.dhat[1], F.dhat[2], w, gx, gy, gz);
       const float dd = F.dhat[0] * gx + F.dhat[1] * gy + F.dhat[2] * gz;
@@ -399,6 +437,22 @@ I4D_D void view_backward(const GaussState& G, const ViewFwd& F, const float4* __
       gmean3[0] += (gx - F.dhat[0] * dd) * idn;
       gmean3[1] += (gy - F.dhat[1] * dd) * idn;
       gmean3[2] += (gz - F.dhat[2] * dd) * idn;
+    }
+    if (nt > 1) {  // SCH coefficients: d raw / d c_mk = cos(2 pi m t) Y_k, summed over views in place
+      float Y1[16];
+      Y1[0] = 1.0f;
+      if constexpr (DEG > 0) sh_basis<DEG>(F.dhat[0], F.dhat[1], F.dhat[2], Y1 + 1);
+      float* gs = reinterpret_cast<float*>(gsch);
+      for (int m = 1; m < nt; ++m) {
+        const float cs = cospif(2.0f * (float)m * C.time);
+#pragma unroll
+        for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            const int idx = sch_index<DEG>(m, k, ch);
+            gs[((size_t)(idx >> 2) * n + gi) * 4 + (idx & 3)] += cs * Y1[k] * graw[ch];
+          }
+      }
     }
   }
 

@@ -40,6 +40,9 @@ static_assert(sizeof(Cam) == sizeof(i4d_camera), "camera layout");
 
 I4D_HD int sh_planes(int deg) { return deg == 0 ? 0 : (deg == 1 ? 3 : (deg == 2 ? 6 : 12)); }
 I4D_HD int sh_coeffs(int deg) { return (deg + 1) * (deg + 1) - 1; }
+// SCH variant: (nt - 1) temporal terms x (deg + 1)^2 harmonics x 3 channels, in planes of 4 floats
+I4D_HD int sch_floats(int deg, int nt) { return nt > 1 ? (nt - 1) * (deg + 1) * (deg + 1) * 3 : 0; }
+I4D_HD int sch_planes(int deg, int nt) { return (sch_floats(deg, nt) + 3) / 4; }
 
 // Which view owns a global tile index (linear scan: at most 64 views, uniform across a block).
 I4D_D int view_of_tile(const ViewTable& vt, int tile) {

@@ -6,12 +6,13 @@
 
 namespace i4d {
 
+// nt > 1: the SCH colour variant with nt - 1 temporal terms (its coefficients after the SH planes)
 cudaError_t launch_slice_project(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
                                  const i4d_camera* cams, const Settings& S, float* proj, uint32_t* touched,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int nt = 0);
 cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
                                      const i4d_camera* cams, const Settings& S, const uint32_t* touched,
-                                     const float* grad2d, float* grads, cudaStream_t st);
+                                     const float* grad2d, float* grads, cudaStream_t st, int nt = 0);
 
 // exclusive scan of n uint32 into out (may alias in); the total goes to *total (int64, device)
 size_t scan_workspace_bytes(int64_t n);

@@ -37,7 +37,8 @@ __device__ __forceinline__ void load_cameras(const ViewTable& vt, const i4d_came
 template <int DEG>
 __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __restrict__ P, int n, int mode, ViewTable vt,
                                                             const i4d_camera* __restrict__ cams, Settings S,
-                                                            float4* __restrict__ proj, uint32_t* __restrict__ touched) {
+                                                            float4* __restrict__ proj, uint32_t* __restrict__ touched,
+                                                            int nt) {
   __shared__ Cam sc[kMaxViews];
   __shared__ ViewExtra sx[kMaxViews];
   load_cameras(vt, cams, sc, sx);
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
   const size_t VN = (size_t)vt.n_views * n;
   for (int v = 0; v < vt.n_views; ++v) {
     ViewFwd F;
-    view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F);
+    view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F, nt);
     uint32_t cnt = 0;
     float4 box = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // empty
     if (F.visible) {
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(128) slice_project_bwd_kernel(const float4* __
                                                                 ViewTable vt, const i4d_camera* __restrict__ cams,
                                                                 Settings S, const uint32_t* __restrict__ touched,
                                                                 const float4* __restrict__ grad2d,
-                                                                float4* __restrict__ grads) {
+                                                                float4* __restrict__ grads, int nt) {
   __shared__ Cam sc[kMaxViews];
   __shared__ ViewExtra sx[kMaxViews];
   load_cameras(vt, cams, sc, sx);
@@ -92,14 +93,18 @@ __global__ void __launch_bounds__(128) slice_project_bwd_kernel(const float4* __
   for (int a = 0; a < NP * 4; ++a) gsh[a] = 0.0f;
   float gA[6] = {0, 0, 0, 0, 0, 0}, gb[3] = {0, 0, 0}, gc = 0.0f;
   const size_t VN = (size_t)vt.n_views * n;
+  // SCH variant: its coefficient gradients are summed over the views in place in this Gaussian's
+  // own entries of the gradient planes (no other thread writes them)
+  float4* gsch = grads + (size_t)(5 + NP) * n;
+  for (int p = 0; p < sch_planes(DEG, nt); ++p) gsch[(size_t)p * n + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (int v = 0; v < vt.n_views; ++v) {
     const size_t r = (size_t)v * n + i;
     if (__ldg(&touched[r]) == 0) continue;
     const float4 g0 = __ldg(&grad2d[r]), g1 = __ldg(&grad2d[VN + r]), g2 = __ldg(&grad2d[2 * VN + r]);
     const float g[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
     ViewFwd F;
-    view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F);
-    view_backward<DEG>(G, F, P + 5 * (size_t)n, n, i, sc[v], g, PG, gsh, gA, gc, gb);
+    view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F, nt);
+    view_backward<DEG>(G, F, P + 5 * (size_t)n, n, i, sc[v], g, PG, gsh, gA, gc, gb, nt, gsch);
   }
   sigma_backward(G, mode, gA, gb, gc, PG);
   grads[i] = make_float4(PG.mu[0], PG.mu[1], PG.mu[2], PG.mu[3]);
@@ -123,24 +128,24 @@ __global__ void __launch_bounds__(128) slice_project_bwd_kernel(const float4* __
 
 cudaError_t launch_slice_project(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
                                  const i4d_camera* cams, const Settings& S, float* proj, uint32_t* touched,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int nt) {
   if (n == 0) return cudaSuccess;
   I4D_PROF("slice_project", st);
   const int threads = 256, blocks = (n + threads - 1) / threads;
   const float4* P = reinterpret_cast<const float4*>(params);
   float4* R = reinterpret_cast<float4*>(proj);
   switch (sh_deg) {
-    case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched); break;
-    case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched); break;
-    case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched); break;
-    default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched); break;
+    case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched, nt); break;
+    case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched, nt); break;
+    case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched, nt); break;
+    default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, R, touched, nt); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int mode, const ViewTable& vt,
                                      const i4d_camera* cams, const Settings& S, const uint32_t* touched,
-                                     const float* grad2d, float* grads, cudaStream_t st) {
+                                     const float* grad2d, float* grads, cudaStream_t st, int nt) {
   if (n == 0) return cudaSuccess;
   I4D_PROF("slice_project_bwd", st);
   const int threads = 128, blocks = (n + threads - 1) / threads;
@@ -148,10 +153,10 @@ cudaError_t launch_slice_project_bwd(const float* params, int n, int sh_deg, int
   const float4* G2 = reinterpret_cast<const float4*>(grad2d);
   float4* GR = reinterpret_cast<float4*>(grads);
   switch (sh_deg) {
-    case 0: slice_project_bwd_kernel<0><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR); break;
-    case 1: slice_project_bwd_kernel<1><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR); break;
-    case 2: slice_project_bwd_kernel<2><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR); break;
-    default: slice_project_bwd_kernel<3><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR); break;
+    case 0: slice_project_bwd_kernel<0><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR, nt); break;
+    case 1: slice_project_bwd_kernel<1><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR, nt); break;
+    case 2: slice_project_bwd_kernel<2><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR, nt); break;
+    default: slice_project_bwd_kernel<3><<<blocks, threads, 0, st>>>(P, n, mode, vt, cams, S, touched, G2, GR, nt); break;
   }
   return cudaGetLastError();
 }

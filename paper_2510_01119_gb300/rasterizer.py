@@ -19,16 +19,22 @@ def sh_planes(deg: int) -> int:
     return {0: 0, 1: 3, 2: 6, 3: 12}[deg]
 
 
-def n_planes(deg: int) -> int:
-    return 5 + sh_planes(deg)
+def sch_planes(deg: int, nt: int) -> int:
+    """Planes of the SCH variant's (nt - 1) x (deg + 1)^2 x 3 coefficients (0 for nt <= 1)."""
+    return ((nt - 1) * (deg + 1) ** 2 * 3 + 3) // 4 if nt > 1 else 0
+
+
+def n_planes(deg: int, nt: int = 0) -> int:
+    return 5 + sh_planes(deg) + sch_planes(deg, nt)
 
 
 def pack_params(g: dict, device="cuda") -> torch.Tensor:
-    """Gaussian dict (mean4 (n,4), logscale4, ql, qr, opacity (n,), rgb (n,3), sh (n,K,3), sh_deg) ->
-    flat float32 tensor of (5 + planes) * n * 4 floats."""
+    """Gaussian dict (mean4 (n,4), logscale4, ql, qr, opacity (n,), rgb (n,3), sh (n,K,3), sh_deg; for the
+    SCH variant also sch_terms N_t and sch (n, N_t - 1, (deg + 1)^2, 3)) -> flat float32 tensor."""
     n = int(np.asarray(g["mean4"]).shape[0])
     deg = int(g.get("sh_deg", 0))
-    planes = np.zeros((n_planes(deg), n, 4), np.float32)
+    nt = int(g.get("sch_terms", 0))
+    planes = np.zeros((n_planes(deg, nt), n, 4), np.float32)
     planes[PLANE_MEAN] = g["mean4"]
     planes[PLANE_SCALE] = g["logscale4"]
     planes[PLANE_QL] = g["ql"]
@@ -39,21 +45,32 @@ def pack_params(g: dict, device="cuda") -> torch.Tensor:
         K = (deg + 1) ** 2 - 1
         flat = np.zeros((n, sh_planes(deg) * 4), np.float32)
         flat[:, :3 * K] = np.asarray(g["sh"], np.float32).reshape(n, 3 * K)
-        planes[PLANE_SH:] = flat.reshape(n, sh_planes(deg), 4).transpose(1, 0, 2)
+        planes[PLANE_SH:PLANE_SH + sh_planes(deg)] = flat.reshape(n, sh_planes(deg), 4).transpose(1, 0, 2)
+    if nt > 1:
+        m = (nt - 1) * (deg + 1) ** 2 * 3
+        flat = np.zeros((n, sch_planes(deg, nt) * 4), np.float32)
+        flat[:, :m] = np.asarray(g["sch"], np.float32).reshape(n, m)
+        planes[PLANE_SH + sh_planes(deg):] = flat.reshape(n, sch_planes(deg, nt), 4).transpose(1, 0, 2)
     return torch.from_numpy(planes.reshape(-1)).to(device)
 
 
-def unpack_params(flat: torch.Tensor, n: int, deg: int) -> dict:
+def unpack_params(flat: torch.Tensor, n: int, deg: int, nt: int = 0) -> dict:
     """Inverse of pack_params (numpy float32 dict, same keys)."""
-    a = flat.detach().cpu().numpy().reshape(n_planes(deg), n, 4)
+    a = flat.detach().cpu().numpy().reshape(n_planes(deg, nt), n, 4)
     out = dict(mean4=a[PLANE_MEAN].copy(), logscale4=a[PLANE_SCALE].copy(), ql=a[PLANE_QL].copy(),
                qr=a[PLANE_QR].copy(), opacity=a[PLANE_ORGB, :, 0].copy(), rgb=a[PLANE_ORGB, :, 1:].copy(),
                sh_deg=deg)
     K = (deg + 1) ** 2 - 1
     if deg > 0:
-        out["sh"] = a[PLANE_SH:].transpose(1, 0, 2).reshape(n, -1)[:, :3 * K].reshape(n, K, 3).copy()
+        out["sh"] = a[PLANE_SH:PLANE_SH + sh_planes(deg)].transpose(1, 0, 2).reshape(n, -1)[:, :3 * K].reshape(
+            n, K, 3).copy()
     else:
         out["sh"] = np.zeros((n, 0, 3), np.float32)
+    if nt > 1:
+        m = (nt - 1) * (deg + 1) ** 2 * 3
+        out["sch_terms"] = nt
+        out["sch"] = a[PLANE_SH + sh_planes(deg):].transpose(1, 0, 2).reshape(n, -1)[:, :m].reshape(
+            n, nt - 1, (deg + 1) ** 2, 3).copy()
     return out
 
 
@@ -75,9 +92,10 @@ class Rasterizer:
     """Owns every device buffer of the forward/backward of one batch of views."""
 
     def __init__(self, n: int, sh_deg: int, mode: int, sizes, tile=(16, 16), capacity: int = None,
-                 settings: dict = None, device="cuda"):
+                 settings: dict = None, device="cuda", sch_terms: int = 0):
         L.load()
         self.n, self.sh_deg, self.mode = int(n), int(sh_deg), int(mode)
+        self.sch_terms = int(sch_terms)
         self.sizes = [(int(w), int(h)) for (w, h) in sizes]
         self.tile = tuple(tile)
         self.device = torch.device(device)
@@ -99,7 +117,8 @@ class Rasterizer:
         self.last = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
         self.n_contrib = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
         self.grad2d = torch.empty(3 * VN * 4, dtype=torch.float32, device=dev)
-        self.grads = torch.empty(n_planes(self.sh_deg) * self.n * 4, dtype=torch.float32, device=dev)
+        self.grads = torch.empty(n_planes(self.sh_deg, self.sch_terms) * self.n * 4, dtype=torch.float32,
+                                 device=dev)
         self._alloc_bins(capacity if capacity else max(1 << 16, 8 * VN))
 
     def _alloc_bins(self, capacity: int):
@@ -111,7 +130,7 @@ class Rasterizer:
     def gaussians(self, params: torch.Tensor) -> L.Gaussians:
         g = L.Gaussians()
         g.params = params.data_ptr()
-        g.n, g.sh_deg, g.mode = self.n, self.sh_deg, self.mode
+        g.n, g.sh_deg, g.mode, g.sch_terms = self.n, self.sh_deg, self.mode, self.sch_terms
         return g
 
     # ---- the three forward calls ----------------------------------------------------------------------

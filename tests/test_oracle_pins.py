@@ -375,6 +375,56 @@ def test_backward_matches_central_differences(orc, mode, cutoffs):
 
 
 # ---------------------------------------------------------------------------------------------
+# SCH appearance variant (Sec. 3.1)
+# ---------------------------------------------------------------------------------------------
+def test_sch_reduces_to_sh_and_matches_closed_forms(orc):
+    C = orc.P
+    g = _fd_scene(31, 12, 0, 1)
+    cam = synth.camera(32, 32, time=0.3)
+    base = orc.project(g, cam)
+    # one temporal term, or all-zero coefficients: exactly the SH colour
+    g1 = dict(g, sch_terms=1)
+    assert np.array_equal(orc.project(g1, cam), base)
+    g3 = dict(g, sch_terms=3, sch=np.zeros((12, 2, 4, 3)))
+    assert np.array_equal(orc.project(g3, cam), base)
+    # the constant harmonic of term m = 2: colour + cos(4 pi t) c
+    g3["sch"][:, 1, 0, :] = 0.05
+    P3 = orc.project(g3, cam)
+    want = base[:, [C["r"], C["g"], C["b"]]] + np.cos(4 * np.pi * np.float32(0.3)) * 0.05
+    np.testing.assert_allclose(P3[:, [C["r"], C["g"], C["b"]]], np.maximum(want, 0), atol=1e-12)
+    # harmonic k = 1 (Y = c1 y with c1 = sqrt(3 / (4 pi))) of term m = 1: + cos(2 pi t) c1 dhat_y c
+    g4 = dict(g, sch_terms=2, sch=np.zeros((12, 1, 4, 3)))
+    g4["sch"][:, 0, 1, 1] = 0.2
+    P4 = orc.project(g4, cam)
+    eye = -np.asarray(cam["R"], np.float64).T @ np.asarray(cam["t"], np.float64)
+    d = P4[:, [C["m3x"], C["m3y"], C["m3z"]]] - eye
+    dy = d[:, 1] / np.linalg.norm(d, axis=1)
+    want_g = base[:, C["g"]] + np.cos(2 * np.pi * np.float32(0.3)) * np.sqrt(3 / (4 * np.pi)) * dy * 0.2
+    np.testing.assert_allclose(P4[:, C["g"]], np.maximum(want_g, 0), atol=1e-12)
+
+
+def test_sch_backward_matches_central_differences(orc):
+    g = _fd_scene(32, 10, 0, 2)
+    g["sch_terms"] = 3
+    g["sch"] = np.random.default_rng(5).normal(0, 0.05, (10, 2, 9, 3))
+    cam = synth.camera(32, 32, time=0.37)
+    S = orc.settings_array(alpha_min=0.0, T_min=0.0, q_max=1e30, ot_min=0.0)
+    w = np.random.default_rng(8).normal(size=(32 * 32, 3))
+    _, grads = orc.render_bwd(g, cam, w, settings=S)
+    h = 1e-6
+    for key, arr in (("sch", g["sch"]), ("mean4", g["mean4"])):
+        for idx in list(np.ndindex(arr.shape))[:: 7 if key == "sch" else 1]:
+            old = arr[idx]
+            arr[idx] = old + h
+            lp, _ = _loss(orc, g, cam, w, S)
+            arr[idx] = old - h
+            lm, _ = _loss(orc, g, cam, w, S)
+            arr[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(grads[key][idx] - fd) <= 2e-6 * max(1.0, abs(fd)), (key, idx, grads[key][idx], fd)
+
+
+# ---------------------------------------------------------------------------------------------
 # tile pairs
 # ---------------------------------------------------------------------------------------------
 def _blendable_tiles(P, i, C, W, H, tile=16):
