@@ -17,7 +17,7 @@ DEFAULT_LR = dict(position=1e-5, position_final=1e-7, time=1e-5, scale=5e-3, rot
                   rgb=2.5e-3, sh=2.5e-3 / 20.0)
 
 
-def adam_groups(n: int, sh_deg: int, steps: int, lr: dict = None):
+def adam_groups(n: int, sh_deg: int, steps: int, lr: dict = None, sch_terms: int = 0):
     lr = dict(DEFAULT_LR, **(lr or {}))
     groups = []
 
@@ -37,6 +37,8 @@ def adam_groups(n: int, sh_deg: int, steps: int, lr: dict = None):
     grp(PLANE_ORGB, PLANE_ORGB + 1, [lr["opacity"], lr["rgb"], lr["rgb"], lr["rgb"]])
     if sh_deg > 0:
         grp(PLANE_SH, n_planes(sh_deg), [lr["sh"]] * 4)
+    if sch_terms > 1:  # the SCH variant's coefficients learn at the SH rate
+        grp(n_planes(sh_deg), n_planes(sh_deg, sch_terms), [lr["sh"]] * 4)
     return groups
 
 
@@ -50,10 +52,10 @@ class TrainStep:
 
     def __init__(self, params: torch.Tensor, n: int, sh_deg: int, mode: int, sizes, steps: int,
                  loss_kind: int = L.LOSS_L1, capacity: int = None, tile=(16, 16), lr: dict = None,
-                 dssim: float = 0.0):
+                 dssim: float = 0.0, sch_terms: int = 0):
         self.params = params
         self.n, self.sh_deg, self.mode = n, sh_deg, mode
-        self.rast = Rasterizer(n, sh_deg, mode, sizes, tile=tile, capacity=capacity)
+        self.rast = Rasterizer(n, sh_deg, mode, sizes, tile=tile, capacity=capacity, sch_terms=sch_terms)
         dev = params.device
         self.m = torch.zeros_like(params)
         self.v = torch.zeros_like(params)
@@ -67,7 +69,7 @@ class TrainStep:
         self.ssim = torch.zeros(1, dtype=torch.float32, device=dev)
         self.loss_ws = (torch.empty(L.i4d_photometric_loss_workspace_size(self.rast.views), dtype=torch.uint8,
                                     device=dev) if self.dssim > 0 else None)
-        self.groups = adam_groups(n, sh_deg, steps, lr)
+        self.groups = adam_groups(n, sh_deg, steps, lr, sch_terms)
         self.graph = None
 
     def run(self):
