@@ -312,11 +312,11 @@ def measured_peaks():
 # ------------------------------------------------------------------------------------------------
 # the other workloads (parity-test cases), timed on request
 # ------------------------------------------------------------------------------------------------
-def _time_render(g_params, n, sh_deg, cams, sizes, dev, reps=20):
+def _time_render(g_params, n, sh_deg, cams, sizes, dev, reps=20, sch_terms=0):
     """ms per render forward + backward (slice_project .. slice_project_bwd) of one batch."""
     import torch
     from paper_2510_01119_gb300 import rasterizer as R
-    rast = R.Rasterizer(n, sh_deg, 0, sizes, device=dev)
+    rast = R.Rasterizer(n, sh_deg, 0, sizes, device=dev, sch_terms=sch_terms)
     rast.forward(g_params, cams)
     rast._alloc_bins(int(1.2 * int(rast.n_inst.item())) + 4096)
     gen = torch.Generator(device=dev).manual_seed(0)
@@ -417,7 +417,10 @@ def run_configs(dev, wl, vid):
                             [(960, 540)], dev)
     npx = 256
     s1 = _time_oracle(g1, cam1, npx, nthr)
-    out["render_200k_sh3_960x540"] = {"gpu_ms_fwd_bwd": ms, "instances": inst,
+    g1s = dict(g1, sch_terms=3, sch=np.random.default_rng(5).normal(0, 0.05, (g1["mean4"].shape[0], 2, 16, 3)))
+    ms_sch, _ = _time_render(R.pack_params(g1s, dev), g1["mean4"].shape[0], 3, R.cameras_tensor([cam1], dev),
+                             [(960, 540)], dev, sch_terms=3)
+    out["render_200k_sh3_960x540"] = {"gpu_ms_fwd_bwd": ms, "instances": inst, "gpu_ms_fwd_bwd_sch3": ms_sch,
                                       "oracle_s_all_threads_extrapolated": s1 * (960 * 540) / npx,
                                       "oracle_sample": f"{npx} pixels, extrapolated linearly", "threads": nthr}
     # the pruned 1.13M scene, 16 views at distinct times: 8 x 480x270 + 8 x 960x540, one launch each
