@@ -11,14 +11,25 @@
 // centre where the fragment can be blended (q <= q_max and alpha >= alpha_min).  A warp stops as soon as all its pixels are saturated (forward) or when
 // it has passed its pixels' last blended fragments (backward).
 // The backward walks the list back to front, recovering the transmittance from T_final by division
-// (no per-fragment state), and sums each Gaussian's nine 2D-gradient components over its half-warp
-// with a transposed shuffle reduction (12 shuffles serve the two halves' Gaussians at once) before
-// nine lanes of the half issue one atomic each.
+// (no per-fragment state).  Per group of up to 16 staged hits of each half it runs two phases: the
+// pixel lanes carry the recurrence and leave two numbers per (pixel, hit) in shared memory, then one
+// lane per hit sums its gradient over the block's 32 pixels in registers and adds the nine components with
+// three vector reductions -- no cross-lane reduction.
 #include "kernels.cuh"
 
 namespace i4d {
 
 namespace {
+
+// Fire-and-forget global float adds: one component, or four consecutive components at a 16-byte
+// aligned address (every record of the 2D-gradient planes starts on 16 bytes; i4d_render_bwd
+// rejects a plane base that does not).
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.v4.f32.add [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
 
 struct TileCoord {
   int v, tx, ty, W, H;
@@ -201,78 +212,31 @@ struct PairBwd {
 
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 
-// Gradient of one fragment at the thread's two pixels, summed over the pixels into g[9] (the 2D
-// record components du, dv, dconic_a, dconic_b, dconic_c, do_t, dr, dg, db).  k0 / k1 say which
-// pixel blended this fragment in the forward; the other lane gets weight 0 and stays unchanged.
-__device__ __forceinline__ void pair_grad(PairBwd& P, float dx, float2 dy, const FragPair& f, bool k0, bool k1,
-                                          const float4& a, const float4& b, float c2, const Settings& S, float* g) {
-  const float2 om = __ffma2_rn(f.alpha, f2(-1.0f), f2(1.0f));
-  const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
-  const float2 niom = __fmul2_rn(iom, f2(-1.0f));
-  const float2 Tk = __fmul2_rn(P.T, iom);  // transmittance in front of this fragment
-  const float2 w = __fmul2_rn(make_float2(k0 ? f.alpha.x : 0.0f, k1 ? f.alpha.y : 0.0f), Tk);
-  // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)), S_c the colour composited behind
-  const float2 xr = __ffma2_rn(Tk, f2(b.z), __fmul2_rn(P.Sr, niom));
-  const float2 xg = __ffma2_rn(Tk, f2(b.w), __fmul2_rn(P.Sg, niom));
-  const float2 xb = __ffma2_rn(Tk, f2(c2), __fmul2_rn(P.Sb, niom));
-  const float2 dA = __ffma2_rn(P.ub, xb, __ffma2_rn(P.ug, xg, __fmul2_rn(P.ur, xr)));
-  const float2 s6 = __fmul2_rn(w, P.ur), s7 = __fmul2_rn(w, P.ug), s8 = __fmul2_rn(w, P.ub);
-  P.Sr = __ffma2_rn(w, f2(b.z), P.Sr);
-  P.Sg = __ffma2_rn(w, f2(b.w), P.Sg);
-  P.Sb = __ffma2_rn(w, f2(c2), P.Sb);
-  P.T = make_float2(k0 ? Tk.x : P.T.x, k1 ? Tk.y : P.T.y);
-  // through alpha = o_t G (zero where the 0.99 cap binds): do_t = dA G, and with
-  // dq = -dA o_t G / 2 = -p / 2: du = p (ca dx + cb dy), dv = p (cb dx + cc dy),
-  // dconic = (dq dx^2, 2 dq dx dy, dq dy^2)
-  const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
-  const float2 dAe = make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f);
-  const float2 s5 = __fmul2_rn(dAe, f.G);
-  const float2 p = __fmul2_rn(f.a_raw, dAe);
-  const float2 s0 = __fmul2_rn(p, __ffma2_rn(f2(a.w), dy, f2(__fmul_rn(a.z, dx))));
-  const float2 s1 = __fmul2_rn(p, __ffma2_rn(f2(b.x), dy, f2(__fmul_rn(a.w, dx))));
-  const float2 s2 = __fmul2_rn(p, f2(__fmul_rn(-0.5f, __fmul_rn(dx, dx))));
-  const float2 s3 = __fmul2_rn(__fmul2_rn(p, f2(-1.0f)), f.dxdy);
-  const float2 s4 = __fmul2_rn(p, __fmul2_rn(f2(-0.5f), f.dydy));
-  g[0] = s0.x + s0.y;
-  g[1] = s1.x + s1.y;
-  g[2] = s2.x + s2.y;
-  g[3] = s3.x + s3.y;
-  g[4] = s4.x + s4.y;
-  g[5] = s5.x + s5.y;
-  g[6] = s6.x + s6.y;
-  g[7] = s7.x + s7.y;
-  g[8] = s8.x + s8.y;
-}
+// The backward runs in two phases per group of up to kGroup = 16 hits of each half.  Phase A (lanes =
+// pixel pairs, hits back to front) carries the per-pixel recurrence -- the transmittance in front
+// of the fragment, the colour composited behind it -- and leaves, for every (pixel, hit) slot, the
+// two numbers the hit's gradient is linear in: s = dL/dalpha G (zero where the fragment was not
+// blended or the 0.99 cap binds) and w = alpha T.  Phase B (lanes = hits) sums them over the
+// block's 32 pixels in registers:
+//   do_t = sum s,  dc = sum w u_c,
+//   du = o_t (ca sum s dx + cb sum s dy),  dv = o_t (cb sum s dx + cc sum s dy),
+//   dconic = -o_t (sum s dx^2 / 2, sum s dx dy, sum s dy^2 / 2)
+// (dL/dq = -dL/dalpha o_t G / 2 = -o_t s / 2), then adds the nine totals to the record's three
+// 2D-gradient planes (components 0-3, 4-7, 8).
+constexpr int kGroup = 16;
 
-// Sum g[0..7] over each 16-lane half so that lane l of a half ends up with the half's total of
-// component (l >> 1) & 7 (both lanes of a pair hold it): 4 + 2 + 1 + 1 = 8 shuffles.
-__device__ __forceinline__ float half_transpose_sum8(const float* g, int lane) {
-  const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float w[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float send = b3 ? g[k] : g[k + 4];
-    const float keep = b3 ? g[k + 4] : g[k];
-    w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float x[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float send = b2 ? w[k] : w[k + 2];
-    const float keep = b2 ? w[k + 2] : w[k];
-    x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  const float send = b1 ? x[0] : x[1];
-  const float keep = b1 ? x[1] : x[0];
-  float y = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  y += __shfl_xor_sync(0xffffffffu, y, 1);
-  return y;
-}
+struct BwdWarp {
+  HalfStage st[2];
+  // (s_upper, s_lower, w_upper, w_lower) of lane j's pixel pair for hit slot k, stored at [j][k ^ j]:
+  // the swizzle keeps both the phase-A stores (fixed k) and the phase-B loads (fixed j) conflict-free
+  float4 sw[2][16][kGroup];
+  float4 urg[2][16];  // upstream gradient of lane j's pair: (r_upper, r_lower, g_upper, g_lower)
+  float2 ub[2][16];   // (b_upper, b_lower)
+};
 
-__device__ __forceinline__ float half_sum(float x) {
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+template <int TW, int TH>
+constexpr size_t bwd_smem_bytes() {
+  return sizeof(BwdWarp) * (TW * TH / 64);
 }
 
 template <int TW, int TH>
@@ -283,14 +247,14 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
                                                                  const uint32_t* __restrict__ last_in,
                                                                  const float* __restrict__ dimg,
                                                                  float* __restrict__ grad2d) {
-  __shared__ HalfStage stage[TW * TH / 64][2];
+  extern __shared__ float4 bwd_smem[];
+  BwdWarp& W = reinterpret_cast<BwdWarp*>(bwd_smem)[threadIdx.x >> 5];
   const int T_all = vt.tile_off[vt.n_views];
   const int tile = (int)ranges[2 * T_all + blockIdx.x];
   const TileCoord tc = tile_coord(vt, tile);
   const WarpPix<TW> wp(tc, TH);
-  const int lane = threadIdx.x & 31;
-  HalfStage* st = stage[threadIdx.x >> 5];
-  const HalfStage& mine = st[wp.half];
+  const int lane = threadIdx.x & 31, l16 = lane & 15;
+  const HalfStage& mine = W.st[wp.half];
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
   const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
@@ -320,51 +284,99 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
     P.ug.y = dimg[pimg + HW];
     P.ub.y = dimg[pimg + 2 * HW];
   }
+  W.urg[wp.half][l16] = make_float4(P.ur.x, P.ur.y, P.ug.x, P.ug.y);
+  W.ub[wp.half][l16] = P.ub;
   P.Sr = __fmul2_rn(P.T, f2(S.bg[0]));
   P.Sg = __fmul2_rn(P.T, f2(S.bg[1]));
   P.Sb = __fmul2_rn(P.T, f2(S.bg[2]));
   // this warp never needs entries past its pixels' last blended fragments
   const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P.L0, P.L1));
   const uint32_t end = rs + min(wL, re - rs);
-  // component c of a 2D-gradient record lives in plane c / 4, lane c % 4 (c = 8: plane 2, lane 0)
-  const int comp = (lane >> 1) & 7;
-  const size_t comp_off = (size_t)(comp >> 2) * VN * 4 + (comp & 3);
-  const bool comp_lane = (lane & 1) == 0;
-  const bool gb_lane = (lane & 15) == 1;
+  // pixel-centre offsets of this half's block: lane j's pair sits in column j & 7, rows 2 (j >> 3) + {0, 1}
+  const float bx0 = wp.hx0, by0 = wp.hy0[wp.half];
+  float4* sw_mine = &W.sw[wp.half][l16][0];
   for (uint32_t hi = end; hi > rs;) {
     const uint32_t lo = (hi - rs > 32u) ? hi - 32u : rs;
     int other;
-    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
-    const int trips = max(cnt, other);  // warp-uniform
-    for (int t = trips - 1; t >= 0; --t) {
-      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool any = false;
-      uint32_t rr = 0;
-      if (t < cnt) {
+    const int cnt = stage_chunk(wp, W.st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
+    for (int ghi = max(cnt, other); ghi > 0; ghi -= kGroup) {  // warp-uniform
+      const int glo = max(ghi - kGroup, 0);
+      // ---- phase A: the recurrence, hits back to front ----
+      unsigned mykept = 0u;  // bit k: hit glo + k blended one of this thread's pixels
+      for (int t = min(ghi, cnt) - 1; t >= glo; --t) {
         const float4 a = mine.a[t];
         const float4 b = mine.b[t];
         const uint4 x = mine.x[t];
         const float c2 = __uint_as_float(x.x);
-        const uint32_t pos = x.y;
-        rr = x.z;
         const float dx = __fsub_rn(fx, a.x);
         const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
         FragPair f;
         eval_pair(dx, dy, a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
         // the fragments a pixel blended are the kept ones before its last (out-of-view pixels: L = 0)
-        const bool k0 = f.k0 && pos < P.L0, k1 = f.k1 && pos < P.L1;
-        any = k0 || k1;
-        if (any) pair_grad(P, dx, dy, f, k0, k1, a, b, c2, S, g);
+        const bool k0 = f.k0 && x.y < P.L0, k1 = f.k1 && x.y < P.L1;
+        mykept |= (k0 || k1 ? 1u : 0u) << (t - glo);
+        const float2 om = __ffma2_rn(f.alpha, f2(-1.0f), f2(1.0f));
+        const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+        const float2 Tk = __fmul2_rn(P.T, iom);  // transmittance in front of this fragment
+        const float2 w = __fmul2_rn(make_float2(k0 ? f.alpha.x : 0.0f, k1 ? f.alpha.y : 0.0f), Tk);
+        // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
+        // S_c the colour composited behind, T the transmittance behind
+        const float2 yr = __ffma2_rn(P.T, f2(b.z), __fmul2_rn(P.Sr, f2(-1.0f)));
+        const float2 yg = __ffma2_rn(P.T, f2(b.w), __fmul2_rn(P.Sg, f2(-1.0f)));
+        const float2 yb = __ffma2_rn(P.T, f2(c2), __fmul2_rn(P.Sb, f2(-1.0f)));
+        const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.ub, yb, __ffma2_rn(P.ug, yg, __fmul2_rn(P.ur, yr))));
+        P.Sr = __ffma2_rn(w, f2(b.z), P.Sr);
+        P.Sg = __ffma2_rn(w, f2(b.w), P.Sg);
+        P.Sb = __ffma2_rn(w, f2(c2), P.Sb);
+        P.T = make_float2(k0 ? Tk.x : P.T.x, k1 ? Tk.y : P.T.y);
+        // alpha = o_t G carries the gradient only below the 0.99 cap
+        const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
+        const float2 s = __fmul2_rn(make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f), f.G);
+        sw_mine[(t - glo) ^ l16] = make_float4(s.x, s.y, w.x, w.y);
       }
-      const unsigned vm = __ballot_sync(0xffffffffu, any);
-      if (vm) {
-        const float tot = half_transpose_sum8(g, lane);
-        const float gb = half_sum(g[8]);
-        if ((vm >> (16 * wp.half)) & 0xffffu) {  // this half has a contribution
-          if (comp_lane) atomicAdd(&grad2d[comp_off + (size_t)rr * 4], tot);
-          if (gb_lane) atomicAdd(&grad2d[2 * VN * 4 + (size_t)rr * 4], gb);
+      const unsigned kept = (__reduce_or_sync(0xffffffffu, mykept << (16 * wp.half)) >> (16 * wp.half)) & 0xffffu;
+      __syncwarp();
+      // ---- phase B: lane k of each half sums hit glo + k of its half over the block's pixel pairs ----
+      const int t = glo + l16;
+      if (t < cnt && t < ghi && ((kept >> l16) & 1u)) {
+        const float4 a = mine.a[t];
+        const float4 b = mine.b[t];
+        const uint32_t rr = mine.x[t].z;
+        float2 dxp[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dxp[c] = f2(__fsub_rn(bx0 + (float)c, a.x));
+        const float2 dyp[2] = {make_float2(__fsub_rn(by0, a.y), __fsub_rn(by0 + 1.0f, a.y)),
+                               make_float2(__fsub_rn(by0 + 2.0f, a.y), __fsub_rn(by0 + 3.0f, a.y))};
+        float2 s0 = f2(0.f), sx = s0, sy = s0, sxx = s0, sxy = s0, syy = s0, ur = s0, ug = s0, ub = s0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float4 v = W.sw[wp.half][j][l16 ^ j];
+          const float4 u = W.urg[wp.half][j];
+          const float2 u3 = W.ub[wp.half][j];
+          const float2 sv = make_float2(v.x, v.y), wv = make_float2(v.z, v.w);
+          const float2 ddx = dxp[j & 7], ddy = dyp[j >> 3];
+          const float2 tx = __fmul2_rn(sv, ddx), ty = __fmul2_rn(sv, ddy);
+          s0 = __fadd2_rn(s0, sv);
+          sx = __fadd2_rn(sx, tx);
+          sy = __fadd2_rn(sy, ty);
+          sxx = __ffma2_rn(tx, ddx, sxx);
+          sxy = __ffma2_rn(tx, ddy, sxy);
+          syy = __ffma2_rn(ty, ddy, syy);
+          ur = __ffma2_rn(wv, make_float2(u.x, u.y), ur);
+          ug = __ffma2_rn(wv, make_float2(u.z, u.w), ug);
+          ub = __ffma2_rn(wv, u3, ub);
         }
+        const float o = b.y;
+        const float Sx = sx.x + sx.y, Sy = sy.x + sy.y;
+        float* g0 = grad2d + (size_t)rr * 4;
+        float* g1 = g0 + VN * 4;
+        float* g2 = g1 + VN * 4;
+        red_add4(g0, o * (a.z * Sx + a.w * Sy), o * (a.w * Sx + b.x * Sy), -0.5f * o * (sxx.x + sxx.y),
+                 -o * (sxy.x + sxy.y));
+        red_add4(g1, -0.5f * o * (syy.x + syy.y), s0.x + s0.y, ur.x + ur.y, ug.x + ug.y);
+        red_add(g2, ub.x + ub.y);
       }
+      __syncwarp();
     }
     __syncwarp();
     hi = lo;
@@ -387,9 +399,13 @@ cudaError_t launch_bwd_t(const ViewTable& vt, int n, const float* proj, const ui
                          const Settings& S, const float* T_final, const uint32_t* last, const float* dL_dimg,
                          float* grad2d, cudaStream_t st) {
   const int tiles = vt.tile_off[vt.n_views];
+  constexpr size_t smem = bwd_smem_bytes<TW, TH>();
+  cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   I4D_PROF("render_bwd", st);
-  render_bwd_kernel<TW, TH><<<tiles, TW * TH / 2, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
-                                                            ranges, S, T_final, last, dL_dimg, grad2d);
+  render_bwd_kernel<TW, TH><<<tiles, TW * TH / 2, smem, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
+                                                               ranges, S, T_final, last, dL_dimg, grad2d);
   return cudaGetLastError();
 }
 
