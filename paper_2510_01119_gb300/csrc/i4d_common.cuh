@@ -77,33 +77,44 @@ I4D_D float blend_q(float ot, const Settings& s) {
   return fminf(s.q_max, fmaxf(qa, 0.0f) + 1e-3f);
 }
 
+// G = exp(-q/2) = 2^(kFalloff q): the compositing kernels stage each conic multiplied by kFalloff so
+// that a fragment's exponent comes straight out of the quadratic form.
+constexpr float kFalloff = -0.72134752044448170368f;  // -log2(e) / 2
+constexpr float kFalloffInv = -1.38629436111989061883f;  // 1 / kFalloff = -2 ln 2
+
+I4D_D float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // One Gaussian evaluated at a thread's two pixels (same column, offsets dx and dy.x / dy.y from the
-// projected mean): q = ca dx^2 + 2 cb dx dy + cc dy^2, the falloff G = exp(-q/2), the raw alpha
-// o_t G and the clamped alpha.  A fragment is kept where q <= q_max and o_t exp(-q/2) >= alpha_min,
-// i.e. where q <= q_thr = min(q_max, 2 ln(o_t / alpha_min)), a per-Gaussian threshold computed once
-// when the entry is staged (one compare per pixel instead of two; the two forms differ only by
-// rounding, well inside the 1e-4 relative margin the parity protocol gives threshold decisions).
-// The pixel pair runs on the packed FP32x2 instructions of sm_100 and later (__fmul2_rn /
-// __ffma2_rn round each lane exactly as __fmul_rn / __fmaf_rn).  The forward and the backward
-// compositing kernels call exactly this code on the same inputs, so they take the same decisions.
+// projected mean), given its conic pre-scaled by kFalloff (sa = kFalloff ca, sb2 = 2 kFalloff cb,
+// sc = kFalloff cc): the exponent m = kFalloff q = sa dx^2 + sb2 dx dy + sc dy^2, the falloff
+// G = 2^m = exp(-q/2), the raw alpha o_t G and the clamped alpha.  A fragment is kept where
+// q <= q_max and o_t exp(-q/2) >= alpha_min, i.e. where m >= m_thr = kFalloff min(q_max, 2 ln(o_t / alpha_min)),
+// a per-Gaussian threshold computed once when the entry is staged (one compare per pixel; the forms
+// differ only by rounding, well inside the 1e-4 relative margin the parity protocol gives threshold
+// decisions).  The pixel pair runs on the packed FP32x2 instructions of sm_100 and later
+// (__fmul2_rn / __ffma2_rn round each lane exactly as __fmul_rn / __fmaf_rn).  The forward and the
+// backward compositing kernels call exactly this code on the same staged values, so they take the
+// same decisions.
 struct FragPair {
-  float2 q, G, a_raw, alpha, dxdy, dydy;
+  float2 G, a_raw, alpha;
   bool k0, k1;
 };
 
-I4D_D void eval_pair(float dx, float2 dy, float ca, float cb, float cc, float ot, float q_thr, const Settings& s,
+I4D_D void eval_pair(float dx, float2 dy, float sa, float sb2, float sc, float ot, float m_thr, const Settings& s,
                      FragPair& f) {
-  const float t0 = __fmul_rn(ca, __fmul_rn(dx, dx));
-  const float c2b = __fmul_rn(2.0f, cb);
-  f.dxdy = __fmul2_rn(make_float2(dx, dx), dy);
-  f.dydy = __fmul2_rn(dy, dy);
-  f.q = __ffma2_rn(make_float2(cc, cc), f.dydy, __ffma2_rn(make_float2(c2b, c2b), f.dxdy, make_float2(t0, t0)));
-  const float2 m = __fmul2_rn(make_float2(-0.5f, -0.5f), f.q);
-  f.G = make_float2(__expf(m.x), __expf(m.y));
+  const float t0 = __fmul_rn(sa, __fmul_rn(dx, dx));
+  const float2 dxdy = __fmul2_rn(make_float2(dx, dx), dy);
+  const float2 dydy = __fmul2_rn(dy, dy);
+  const float2 m = __ffma2_rn(make_float2(sc, sc), dydy, __ffma2_rn(make_float2(sb2, sb2), dxdy, make_float2(t0, t0)));
+  f.G = make_float2(ex2_approx(m.x), ex2_approx(m.y));
   f.a_raw = __fmul2_rn(make_float2(ot, ot), f.G);
   f.alpha = make_float2(fminf(s.alpha_max, f.a_raw.x), fminf(s.alpha_max, f.a_raw.y));
-  f.k0 = f.q.x <= q_thr;
-  f.k1 = f.q.y <= q_thr;
+  f.k0 = m.x >= m_thr;
+  f.k1 = m.y >= m_thr;
 }
 
 // Pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_max of a conic, widened by

@@ -71,11 +71,24 @@ struct WarpPix {
   }
 };
 
+// The staged form of a record: mean, conic pre-scaled by kFalloff (see eval_pair), opacity, colour,
+// list position, record index and the exponent threshold of the kept test.
+__device__ __forceinline__ void stage_entry(const float4* __restrict__ proj, size_t VN, uint32_t r, uint32_t pos,
+                                            const Settings& S, float4& a, float4& b, uint4& x) {
+  const float4 pa = __ldg(&proj[r]);
+  const float4 pb = __ldg(&proj[VN + r]);
+  const float c2 = __ldg(&proj[2 * VN + r]).x;
+  const float q_thr = fminf(S.q_max, 2.0f * logf(pb.y / S.alpha_min));
+  a = make_float4(pa.x, pa.y, __fmul_rn(kFalloff, pa.z), __fmul_rn(2.0f * kFalloff, pa.w));
+  b = make_float4(__fmul_rn(kFalloff, pb.x), pb.y, pb.z, pb.w);
+  x = make_uint4(__float_as_uint(c2), pos, r, __float_as_uint(__fmul_rn(kFalloff, q_thr)));
+}
+
 // A half-warp's staged hits of one chunk.
 struct HalfStage {
   float4 a[32];
   float4 b[32];
-  uint4 x[32];  // (colour b bits, list position, record, q threshold bits)
+  uint4 x[32];  // (colour b bits, list position, record, exponent threshold bits)
 };
 
 // Stage the chunk [lo, hi) of the tile list: every lane tests one entry against both halves' blocks
@@ -97,12 +110,9 @@ __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const fl
   const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
   if (hit0 || hit1) {
     const unsigned lt = (1u << lane) - 1u;
-    const float4 a = __ldg(&proj[r]);
-    const float4 b = __ldg(&proj[VN + r]);
-    const float c2 = __ldg(&proj[2 * VN + r]).x;
-    const uint32_t pos = idx - tile_start;
-    const float q_thr = fminf(S.q_max, 2.0f * logf(b.y / S.alpha_min));
-    const uint4 x = make_uint4(__float_as_uint(c2), pos, r, __float_as_uint(q_thr));
+    float4 a, b;
+    uint4 x;
+    stage_entry(proj, VN, r, idx - tile_start, S, a, b, x);
     if (hit0) {
       const int k = __popc(m0 & lt);
       st[0].a[k] = a; st[0].b[k] = b; st[0].x[k] = x;
@@ -111,6 +121,43 @@ __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const fl
       const int k = __popc(m1 & lt);
       st[1].a[k] = a; st[1].b[k] = b; st[1].x[k] = x;
     }
+  }
+  __syncwarp();
+  other = __popc(wp.half ? m0 : m1);
+  return __popc(wp.half ? m1 : m0);
+}
+
+// The backward's staging: the chunk's entries that hit either half, stored once in list order, and
+// per half the positions of its hits among them (a hit of both halves is staged once).
+struct SharedStage {
+  float4 a[32];
+  float4 b[32];
+  uint4 x[32];  // (colour b bits, list position, record, exponent threshold bits)
+  uint8_t idx[2][32];
+};
+
+template <class WP>
+__device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st, const float4* __restrict__ proj,
+                                                  size_t VN, const uint32_t* __restrict__ ids, uint32_t vbase,
+                                                  uint32_t lo, uint32_t hi, uint32_t tile_start, int lane, int& other,
+                                                  const Settings& S) {
+  const uint32_t idx = lo + lane;
+  uint32_t r = 0;
+  bool hit0 = false, hit1 = false;
+  if (idx < hi) {
+    r = vbase + __ldg(&ids[idx]);
+    const float4 box = __ldg(&proj[3 * VN + r]);
+    hit0 = !wp.misses(box, 0);
+    hit1 = !wp.misses(box, 1);
+  }
+  const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+  const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+  if (hit0 || hit1) {
+    const unsigned lt = (1u << lane) - 1u;
+    const int k = __popc((m0 | m1) & lt);
+    stage_entry(proj, VN, r, idx - tile_start, S, st.a[k], st.b[k], st.x[k]);
+    if (hit0) st.idx[0][__popc(m0 & lt)] = (uint8_t)k;
+    if (hit1) st.idx[1][__popc(m1 & lt)] = (uint8_t)k;
   }
   __syncwarp();
   other = __popc(wp.half ? m0 : m1);
@@ -203,10 +250,10 @@ __global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, i
 }
 
 // Backward state of the thread's two pixels (float2 lanes): transmittance in front of the next
-// (nearer) fragment, colour composited behind it, upstream gradient, and the positions of the
-// pixels' last blended fragments.
+// (nearer) fragment, the negated colour composited behind it, upstream gradient, and the positions
+// of the pixels' last blended fragments.
 struct PairBwd {
-  float2 T, Sr, Sg, Sb, ur, ug, ub;
+  float2 T, NSr, NSg, NSb, ur, ug, ub;
   uint32_t L0, L1;
 };
 
@@ -216,18 +263,19 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 // pixel pairs, hits back to front) carries the per-pixel recurrence -- the transmittance in front
 // of the fragment, the colour composited behind it -- and leaves, for every (pixel, hit) slot, the
 // two numbers the hit's gradient is linear in: s = dL/dalpha G (zero where the fragment was not
-// blended or the 0.99 cap binds) and w = alpha T.  Phase B (lanes = hits) sums them over the
+// blended or the 0.99 cap binds) and -w = -alpha T.  Phase B (lanes = hits) sums them over the
 // block's 32 pixels in registers:
 //   do_t = sum s,  dc = sum w u_c,
 //   du = o_t (ca sum s dx + cb sum s dy),  dv = o_t (cb sum s dx + cc sum s dy),
 //   dconic = -o_t (sum s dx^2 / 2, sum s dx dy, sum s dy^2 / 2)
 // (dL/dq = -dL/dalpha o_t G / 2 = -o_t s / 2), then adds the nine totals to the record's three
-// 2D-gradient planes (components 0-3, 4-7, 8).
+// 2D-gradient planes (components 0-3, 4-7, 8).  Phase A carries S negated and stores -w, which
+// saves the negations in dL/dalpha; phase B flips the colour totals back.
 constexpr int kGroup = 16;
 
 struct BwdWarp {
-  HalfStage st[2];
-  // (s_upper, s_lower, w_upper, w_lower) of lane j's pixel pair for hit slot k, stored at [j][k ^ j]:
+  SharedStage st;
+  // (s_upper, s_lower, -w_upper, -w_lower) of lane j's pixel pair for hit slot k, stored at [j][k ^ j]:
   // the swizzle keeps both the phase-A stores (fixed k) and the phase-B loads (fixed j) conflict-free
   float4 sw[2][16][kGroup];
   float4 urg[2][16];  // upstream gradient of lane j's pair: (r_upper, r_lower, g_upper, g_lower)
@@ -239,8 +287,15 @@ constexpr size_t bwd_smem_bytes() {
   return sizeof(BwdWarp) * (TW * TH / 64);
 }
 
+// Resident CTAs per SM the backward is compiled for: 20 warps (10.3 KB of shared memory each),
+// which caps the registers at 102 per thread.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
+constexpr int bwd_min_blocks() {
+  return (TW * TH / 64) >= 20 ? 1 : 20 / (TW * TH / 64);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_bwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ ranges, Settings S,
                                                                  const float* __restrict__ T_final,
@@ -254,7 +309,8 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   const TileCoord tc = tile_coord(vt, tile);
   const WarpPix<TW> wp(tc, TH);
   const int lane = threadIdx.x & 31, l16 = lane & 15;
-  const HalfStage& mine = W.st[wp.half];
+  const SharedStage& stg = W.st;
+  const uint8_t* my_idx = W.st.idx[wp.half];
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
   const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
@@ -264,7 +320,7 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   const float2 fy = make_float2((float)wp.py0 + 0.5f, (float)wp.py0 + 1.5f);
   const int64_t HW = (int64_t)tc.W * tc.H;
   PairBwd P;
-  P.T = P.Sr = P.Sg = P.Sb = P.ur = P.ug = P.ub = f2(0.0f);
+  P.T = P.NSr = P.NSg = P.NSb = P.ur = P.ug = P.ub = f2(0.0f);
   P.L0 = P.L1 = 0u;
   if (in0) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
@@ -286,9 +342,9 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   }
   W.urg[wp.half][l16] = make_float4(P.ur.x, P.ur.y, P.ug.x, P.ug.y);
   W.ub[wp.half][l16] = P.ub;
-  P.Sr = __fmul2_rn(P.T, f2(S.bg[0]));
-  P.Sg = __fmul2_rn(P.T, f2(S.bg[1]));
-  P.Sb = __fmul2_rn(P.T, f2(S.bg[2]));
+  P.NSr = __fmul2_rn(P.T, f2(-S.bg[0]));
+  P.NSg = __fmul2_rn(P.T, f2(-S.bg[1]));
+  P.NSb = __fmul2_rn(P.T, f2(-S.bg[2]));
   // this warp never needs entries past its pixels' last blended fragments
   const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P.L0, P.L1));
   const uint32_t end = rs + min(wL, re - rs);
@@ -298,50 +354,50 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
   for (uint32_t hi = end; hi > rs;) {
     const uint32_t lo = (hi - rs > 32u) ? hi - 32u : rs;
     int other;
-    const int cnt = stage_chunk(wp, W.st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
+    const int cnt = stage_chunk_shared(wp, W.st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
     for (int ghi = max(cnt, other); ghi > 0; ghi -= kGroup) {  // warp-uniform
       const int glo = max(ghi - kGroup, 0);
       // ---- phase A: the recurrence, hits back to front ----
-      unsigned mykept = 0u;  // bit k: hit glo + k blended one of this thread's pixels
       for (int t = min(ghi, cnt) - 1; t >= glo; --t) {
-        const float4 a = mine.a[t];
-        const float4 b = mine.b[t];
-        const uint4 x = mine.x[t];
-        const float c2 = __uint_as_float(x.x);
+        const int e = my_idx[t];
+        const float4 a = stg.a[e];
+        const float4 b = stg.b[e];
+        const uint4 x = stg.x[e];
         const float dx = __fsub_rn(fx, a.x);
         const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
         FragPair f;
         eval_pair(dx, dy, a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
         // the fragments a pixel blended are the kept ones before its last (out-of-view pixels: L = 0)
         const bool k0 = f.k0 && x.y < P.L0, k1 = f.k1 && x.y < P.L1;
-        mykept |= (k0 || k1 ? 1u : 0u) << (t - glo);
-        const float2 om = __ffma2_rn(f.alpha, f2(-1.0f), f2(1.0f));
+        const float2 na = __fmul2_rn(f.alpha, f2(-1.0f));
+        const float2 om = __fadd2_rn(na, f2(1.0f));
         const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
         const float2 Tk = __fmul2_rn(P.T, iom);  // transmittance in front of this fragment
-        const float2 w = __fmul2_rn(make_float2(k0 ? f.alpha.x : 0.0f, k1 ? f.alpha.y : 0.0f), Tk);
+        const float2 nw = __fmul2_rn(make_float2(k0 ? na.x : 0.0f, k1 ? na.y : 0.0f), Tk);  // -alpha T_k
         // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
         // S_c the colour composited behind, T the transmittance behind
-        const float2 yr = __ffma2_rn(P.T, f2(b.z), __fmul2_rn(P.Sr, f2(-1.0f)));
-        const float2 yg = __ffma2_rn(P.T, f2(b.w), __fmul2_rn(P.Sg, f2(-1.0f)));
-        const float2 yb = __ffma2_rn(P.T, f2(c2), __fmul2_rn(P.Sb, f2(-1.0f)));
+        const float2 cr = f2(b.z), cg = f2(b.w), cb = f2(__uint_as_float(x.x));
+        const float2 yr = __ffma2_rn(P.T, cr, P.NSr);
+        const float2 yg = __ffma2_rn(P.T, cg, P.NSg);
+        const float2 yb = __ffma2_rn(P.T, cb, P.NSb);
         const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.ub, yb, __ffma2_rn(P.ug, yg, __fmul2_rn(P.ur, yr))));
-        P.Sr = __ffma2_rn(w, f2(b.z), P.Sr);
-        P.Sg = __ffma2_rn(w, f2(b.w), P.Sg);
-        P.Sb = __ffma2_rn(w, f2(c2), P.Sb);
+        P.NSr = __ffma2_rn(nw, cr, P.NSr);
+        P.NSg = __ffma2_rn(nw, cg, P.NSg);
+        P.NSb = __ffma2_rn(nw, cb, P.NSb);
         P.T = make_float2(k0 ? Tk.x : P.T.x, k1 ? Tk.y : P.T.y);
         // alpha = o_t G carries the gradient only below the 0.99 cap
         const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
-        const float2 s = __fmul2_rn(make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f), f.G);
-        sw_mine[(t - glo) ^ l16] = make_float4(s.x, s.y, w.x, w.y);
+        const float2 sv = __fmul2_rn(make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f), f.G);
+        sw_mine[(t - glo) ^ l16] = make_float4(sv.x, sv.y, nw.x, nw.y);
       }
-      const unsigned kept = (__reduce_or_sync(0xffffffffu, mykept << (16 * wp.half)) >> (16 * wp.half)) & 0xffffu;
       __syncwarp();
       // ---- phase B: lane k of each half sums hit glo + k of its half over the block's pixel pairs ----
       const int t = glo + l16;
-      if (t < cnt && t < ghi && ((kept >> l16) & 1u)) {
-        const float4 a = mine.a[t];
-        const float4 b = mine.b[t];
-        const uint32_t rr = mine.x[t].z;
+      if (t < cnt && t < ghi) {
+        const int e = my_idx[t];
+        const float4 a = stg.a[e];
+        const float4 b = stg.b[e];
+        const uint32_t rr = stg.x[e].z;
         float2 dxp[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) dxp[c] = f2(__fsub_rn(bx0 + (float)c, a.x));
@@ -353,7 +409,7 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
           const float4 v = W.sw[wp.half][j][l16 ^ j];
           const float4 u = W.urg[wp.half][j];
           const float2 u3 = W.ub[wp.half][j];
-          const float2 sv = make_float2(v.x, v.y), wv = make_float2(v.z, v.w);
+          const float2 sv = make_float2(v.x, v.y), nwv = make_float2(v.z, v.w);
           const float2 ddx = dxp[j & 7], ddy = dyp[j >> 3];
           const float2 tx = __fmul2_rn(sv, ddx), ty = __fmul2_rn(sv, ddy);
           s0 = __fadd2_rn(s0, sv);
@@ -362,19 +418,28 @@ __global__ void __launch_bounds__(TW * TH / 2) render_bwd_kernel(ViewTable vt, i
           sxx = __ffma2_rn(tx, ddx, sxx);
           sxy = __ffma2_rn(tx, ddy, sxy);
           syy = __ffma2_rn(ty, ddy, syy);
-          ur = __ffma2_rn(wv, make_float2(u.x, u.y), ur);
-          ug = __ffma2_rn(wv, make_float2(u.z, u.w), ug);
-          ub = __ffma2_rn(wv, u3, ub);
+          ur = __ffma2_rn(nwv, make_float2(u.x, u.y), ur);
+          ug = __ffma2_rn(nwv, make_float2(u.z, u.w), ug);
+          ub = __ffma2_rn(nwv, u3, ub);
         }
-        const float o = b.y;
+        // the staged conic is scaled by kFalloff (see eval_pair); o_t (ca Sx + cb Sy) etc. need it plain
+        const float o = b.y, ca = kFalloffInv * a.z, cb = 0.5f * kFalloffInv * a.w, cc = kFalloffInv * b.x;
         const float Sx = sx.x + sx.y, Sy = sy.x + sy.y;
-        float* g0 = grad2d + (size_t)rr * 4;
-        float* g1 = g0 + VN * 4;
-        float* g2 = g1 + VN * 4;
-        red_add4(g0, o * (a.z * Sx + a.w * Sy), o * (a.w * Sx + b.x * Sy), -0.5f * o * (sxx.x + sxx.y),
-                 -o * (sxy.x + sxy.y));
-        red_add4(g1, -0.5f * o * (syy.x + syy.y), s0.x + s0.y, ur.x + ur.y, ug.x + ug.y);
-        red_add(g2, ub.x + ub.y);
+        const float g[9] = {o * (ca * Sx + cb * Sy), o * (cb * Sx + cc * Sy), -0.5f * o * (sxx.x + sxx.y),
+                            -o * (sxy.x + sxy.y), -0.5f * o * (syy.x + syy.y), s0.x + s0.y,
+                            -(ur.x + ur.y), -(ug.x + ug.y), -(ub.x + ub.y)};
+        // a hit that blended none of the block's pixels has all nine totals zero; adding zeros
+        // changes nothing, so such hits issue no reductions
+        bool nz = false;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) nz = nz || g[c] != 0.0f;
+        if (nz) {
+          float* g0 = grad2d + (size_t)rr * 4;
+          float* g1 = g0 + VN * 4;
+          red_add4(g0, g[0], g[1], g[2], g[3]);
+          red_add4(g1, g[4], g[5], g[6], g[7]);
+          red_add(g1 + VN * 4, g[8]);
+        }
       }
       __syncwarp();
     }
