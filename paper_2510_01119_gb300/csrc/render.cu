@@ -8,13 +8,14 @@
 // the blocks of its two halves, and stages the hits of each half -- compacted in list order by a
 // ballot and a prefix count -- in that half's shared-memory slots; each half's pixels then visit
 // only those hits, the two halves side by side.  The test is exact: the box holds every pixel
-// centre where the fragment can be blended (q <= q_max and alpha >= alpha_min).  A warp stops as soon as all its pixels are saturated (forward) or when
-// it has passed its pixels' last blended fragments (backward).
+// centre where the fragment can be blended (q <= q_max and alpha >= alpha_min).  A warp stops as
+// soon as all its pixels are saturated (forward) or when it has passed its pixels' last blended
+// fragments (backward).
 // The backward walks the list back to front, recovering the transmittance from T_final by division
 // (no per-fragment state).  Per group of up to 16 staged hits of each half it runs two phases: the
-// pixel lanes carry the recurrence and leave two numbers per (pixel, hit) in shared memory, then one
-// lane per hit sums its gradient over the block's 32 pixels in registers and adds the nine components with
-// three vector reductions -- no cross-lane reduction.
+// pixel lanes carry the recurrence and leave two numbers per (pixel, hit) in shared memory, then
+// one to four lanes per hit sum its gradient over the block's 32 pixels in registers and add the
+// nine components with three vector reductions -- no reduction across the pixel lanes.
 #include "kernels.cuh"
 
 namespace i4d {
@@ -264,7 +265,7 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 // of the fragment, the colour composited behind it -- and leaves, for every (pixel, hit) slot, the
 // two numbers the hit's gradient is linear in: s = dL/dalpha G (zero where the fragment was not
 // blended or the 0.99 cap binds) and -w = -alpha T.  Phase B (lanes = hits) sums them over the
-// block's 32 pixels in registers:
+// block's 32 pixels in registers (1, 2 or 4 lanes per hit by the group's size):
 //   do_t = sum s,  dc = sum w u_c,
 //   du = o_t (ca sum s dx + cb sum s dy),  dv = o_t (cb sum s dx + cc sum s dy),
 //   dconic = -o_t (sum s dx^2 / 2, sum s dx dy, sum s dy^2 / 2)
@@ -273,18 +274,135 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 // saves the negations in dL/dalpha; phase B flips the colour totals back.
 constexpr int kGroup = 16;
 
+// Placement of pixel pair q's entries: with z(q) = (q & 7) ^ 6 (q >> 3), the 16-byte slots that one
+// quarter-warp touches fall in distinct bank groups for every access pattern of the two phases --
+// phase A (fixed hit, q = 0..7 or 8..15) and phase B with 1, 2 or 4 lanes per hit (hits k and pairs
+// q = i; q = i, 8 + i; q = i, 4 + i, 8 + i, 12 + i).
+__device__ __forceinline__ int pair_swz(int q) { return (q & 7) ^ (6 * (q >> 3)); }
+
 struct BwdWarp {
   SharedStage st;
-  // (s_upper, s_lower, -w_upper, -w_lower) of lane j's pixel pair for hit slot k, stored at [j][k ^ j]:
-  // the swizzle keeps both the phase-A stores (fixed k) and the phase-B loads (fixed j) conflict-free
+  // (s_upper, s_lower, -w_upper, -w_lower) of pixel pair q for hit slot k, at [q][k ^ pair_swz(q)]
   float4 sw[2][16][kGroup];
-  float4 urg[2][16];  // upstream gradient of lane j's pair: (r_upper, r_lower, g_upper, g_lower)
-  float2 ub[2][16];   // (b_upper, b_lower)
+  float4 urg[2][16];  // upstream gradient of pair q at [(q & 8) | pair_swz(q)]: (r_up, r_low, g_up, g_low)
+  float2 ub[2][16];   // (b_upper, b_lower) of pair q
 };
 
 template <int TW, int TH>
 constexpr size_t bwd_smem_bytes() {
   return sizeof(BwdWarp) * (TW * TH / 64);
+}
+
+// One hit's nine sums over (part of) its block: sum s, sum s dx, sum s dy, sum s dx^2, sum s dx dy,
+// sum s dy^2 and sum_c (-w) u_c, with (dx, dy) the pixel centre minus the projected mean.
+struct HitSums {
+  float s0, sx, sy, sxx, sxy, syy, cr, cg, cb;
+};
+
+// Adds to h the sums of hit slot k over NK consecutive pixel pairs q = qb .. qb + NK - 1 of one row
+// pair.  The pairs' columns are c0 + i (i = 0 .. NK - 1) and their rows r0 and r0 + 1, so with
+// cx = x(c0) - u and cy = y(r0) - v the offsets are dx = i + cx, dy = {0, 1} + cy: the loop only
+// accumulates sum s, sum i s and sum i^2 s (per row, packed) with i a compile-time constant, and the
+// offsets enter once at the end.
+template <int NK>
+__device__ __forceinline__ void seg_sums(const float4 (*sw)[kGroup], const float4* urg, const float2* ub, int qb,
+                                         int k, float cx, float cy, HitSums& h) {
+  float2 A = f2(0.0f), B = A, C = A, ur = A, ug = A, uB = A;
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int q = qb + i;
+    const int z = pair_swz(q);
+    const float4 v = sw[q][k ^ z];
+    const float4 u = urg[(q & 8) | z];
+    const float2 u3 = ub[q];
+    const float2 sv = make_float2(v.x, v.y), nwv = make_float2(v.z, v.w);
+    A = __fadd2_rn(A, sv);
+    if (i == 1) {
+      B = __fadd2_rn(B, sv);
+      C = __fadd2_rn(C, sv);
+    } else if (i > 1) {
+      B = __ffma2_rn(sv, f2((float)i), B);
+      C = __ffma2_rn(sv, f2((float)(i * i)), C);
+    }
+    ur = __ffma2_rn(nwv, make_float2(u.x, u.y), ur);
+    ug = __ffma2_rn(nwv, make_float2(u.z, u.w), ug);
+    uB = __ffma2_rn(nwv, u3, uB);
+  }
+  // sum s (i + cx)^j (r + cy)^l with r in {0, 1} the row within the pair (r^2 = r)
+  const float a = A.x + A.y, ay = A.y, b = B.x + B.y, by = B.y, c = C.x + C.y;
+  h.s0 += a;
+  h.sx += fmaf(cx, a, b);
+  h.sy += fmaf(cy, a, ay);
+  h.sxx += fmaf(cx, fmaf(cx, a, 2.0f * b), c);
+  h.sxy += fmaf(cx, fmaf(cy, a, ay), fmaf(cy, b, by));
+  h.syy += fmaf(cy, fmaf(cy, a, 2.0f * ay), ay);
+  h.cr += ur.x + ur.y;
+  h.cg += ug.x + ug.y;
+  h.cb += uB.x + uB.y;
+}
+
+__device__ __forceinline__ void hit_sums_xor(HitSums& h, int m) {
+  h.s0 += __shfl_xor_sync(0xffffffffu, h.s0, m);
+  h.sx += __shfl_xor_sync(0xffffffffu, h.sx, m);
+  h.sy += __shfl_xor_sync(0xffffffffu, h.sy, m);
+  h.sxx += __shfl_xor_sync(0xffffffffu, h.sxx, m);
+  h.sxy += __shfl_xor_sync(0xffffffffu, h.sxy, m);
+  h.syy += __shfl_xor_sync(0xffffffffu, h.syy, m);
+  h.cr += __shfl_xor_sync(0xffffffffu, h.cr, m);
+  h.cg += __shfl_xor_sync(0xffffffffu, h.cg, m);
+  h.cb += __shfl_xor_sync(0xffffffffu, h.cb, m);
+}
+
+// Phase B with S lanes per hit (S = 1, 2 or 4; 16 / S hits of each half at most): lane l of a half
+// takes hit slot l / S and the S-th part l % S of the block's 16 pixel pairs (S = 1: both row
+// pairs; S = 2: row pair l % 2; S = 4: half a row pair), then the S lanes of a hit add their sums
+// and the first issues the hit's three reductions.
+template <int S>
+__device__ __forceinline__ void phase_b(const BwdWarp& W, int half, int l16, int hc, int glo, const uint8_t* my_idx,
+                                        float bx0, float by0, size_t VN, float* __restrict__ grad2d) {
+  const int k = l16 / S, part = l16 % S;
+  const bool valid = k < hc;
+  HitSums h = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+  uint32_t rr = 0;
+  if (valid) {
+    const int e = my_idx[glo + k];
+    a = W.st.a[e];
+    b = W.st.b[e];
+    rr = W.st.x[e].z;
+    const float4(*sw)[kGroup] = W.sw[half];
+    if (S == 1) {
+      const float cx = __fsub_rn(bx0, a.x);
+      seg_sums<8>(sw, W.urg[half], W.ub[half], 0, k, cx, __fsub_rn(by0, a.y), h);
+      seg_sums<8>(sw, W.urg[half], W.ub[half], 8, k, cx, __fsub_rn(by0 + 2.0f, a.y), h);
+    } else if (S == 2) {
+      seg_sums<8>(sw, W.urg[half], W.ub[half], 8 * part, k, __fsub_rn(bx0, a.x),
+                  __fsub_rn(by0 + (float)(2 * part), a.y), h);
+    } else {
+      seg_sums<4>(sw, W.urg[half], W.ub[half], 4 * part, k, __fsub_rn(bx0 + (float)(4 * (part & 1)), a.x),
+                  __fsub_rn(by0 + (float)(2 * (part >> 1)), a.y), h);
+    }
+  }
+  if (S >= 2) hit_sums_xor(h, 1);
+  if (S >= 4) hit_sums_xor(h, 2);
+  if (valid && part == 0) {
+    // the staged conic is scaled by kFalloff (see eval_pair); the gradients need it plain
+    const float o = b.y, ca = kFalloffInv * a.z, cb = 0.5f * kFalloffInv * a.w, cc = kFalloffInv * b.x;
+    const float g[9] = {o * (ca * h.sx + cb * h.sy), o * (cb * h.sx + cc * h.sy), -0.5f * o * h.sxx, -o * h.sxy,
+                        -0.5f * o * h.syy, h.s0, -h.cr, -h.cg, -h.cb};
+    // a hit that blended none of the block's pixels has all nine totals zero; adding zeros changes
+    // nothing, so such hits issue no reductions
+    bool nz = false;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) nz = nz || g[c] != 0.0f;
+    if (nz) {
+      float* g0 = grad2d + (size_t)rr * 4;
+      float* g1 = g0 + VN * 4;
+      red_add4(g0, g[0], g[1], g[2], g[3]);
+      red_add4(g1, g[4], g[5], g[6], g[7]);
+      red_add(g1 + VN * 4, g[8]);
+    }
+  }
 }
 
 // Resident CTAs per SM the backward is compiled for: 20 warps (10.3 KB of shared memory each),
@@ -340,7 +458,8 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
     P.ug.y = dimg[pimg + HW];
     P.ub.y = dimg[pimg + 2 * HW];
   }
-  W.urg[wp.half][l16] = make_float4(P.ur.x, P.ur.y, P.ug.x, P.ug.y);
+  const int zl = pair_swz(l16);
+  W.urg[wp.half][(l16 & 8) | zl] = make_float4(P.ur.x, P.ur.y, P.ug.x, P.ug.y);
   W.ub[wp.half][l16] = P.ub;
   P.NSr = __fmul2_rn(P.T, f2(-S.bg[0]));
   P.NSg = __fmul2_rn(P.T, f2(-S.bg[1]));
@@ -388,59 +507,18 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
         // alpha = o_t G carries the gradient only below the 0.99 cap
         const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
         const float2 sv = __fmul2_rn(make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f), f.G);
-        sw_mine[(t - glo) ^ l16] = make_float4(sv.x, sv.y, nw.x, nw.y);
+        sw_mine[(t - glo) ^ zl] = make_float4(sv.x, sv.y, nw.x, nw.y);
       }
       __syncwarp();
-      // ---- phase B: lane k of each half sums hit glo + k of its half over the block's pixel pairs ----
-      const int t = glo + l16;
-      if (t < cnt && t < ghi) {
-        const int e = my_idx[t];
-        const float4 a = stg.a[e];
-        const float4 b = stg.b[e];
-        const uint32_t rr = stg.x[e].z;
-        float2 dxp[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) dxp[c] = f2(__fsub_rn(bx0 + (float)c, a.x));
-        const float2 dyp[2] = {make_float2(__fsub_rn(by0, a.y), __fsub_rn(by0 + 1.0f, a.y)),
-                               make_float2(__fsub_rn(by0 + 2.0f, a.y), __fsub_rn(by0 + 3.0f, a.y))};
-        float2 s0 = f2(0.f), sx = s0, sy = s0, sxx = s0, sxy = s0, syy = s0, ur = s0, ug = s0, ub = s0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float4 v = W.sw[wp.half][j][l16 ^ j];
-          const float4 u = W.urg[wp.half][j];
-          const float2 u3 = W.ub[wp.half][j];
-          const float2 sv = make_float2(v.x, v.y), nwv = make_float2(v.z, v.w);
-          const float2 ddx = dxp[j & 7], ddy = dyp[j >> 3];
-          const float2 tx = __fmul2_rn(sv, ddx), ty = __fmul2_rn(sv, ddy);
-          s0 = __fadd2_rn(s0, sv);
-          sx = __fadd2_rn(sx, tx);
-          sy = __fadd2_rn(sy, ty);
-          sxx = __ffma2_rn(tx, ddx, sxx);
-          sxy = __ffma2_rn(tx, ddy, sxy);
-          syy = __ffma2_rn(ty, ddy, syy);
-          ur = __ffma2_rn(nwv, make_float2(u.x, u.y), ur);
-          ug = __ffma2_rn(nwv, make_float2(u.z, u.w), ug);
-          ub = __ffma2_rn(nwv, u3, ub);
-        }
-        // the staged conic is scaled by kFalloff (see eval_pair); o_t (ca Sx + cb Sy) etc. need it plain
-        const float o = b.y, ca = kFalloffInv * a.z, cb = 0.5f * kFalloffInv * a.w, cc = kFalloffInv * b.x;
-        const float Sx = sx.x + sx.y, Sy = sy.x + sy.y;
-        const float g[9] = {o * (ca * Sx + cb * Sy), o * (cb * Sx + cc * Sy), -0.5f * o * (sxx.x + sxx.y),
-                            -o * (sxy.x + sxy.y), -0.5f * o * (syy.x + syy.y), s0.x + s0.y,
-                            -(ur.x + ur.y), -(ug.x + ug.y), -(ub.x + ub.y)};
-        // a hit that blended none of the block's pixels has all nine totals zero; adding zeros
-        // changes nothing, so such hits issue no reductions
-        bool nz = false;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) nz = nz || g[c] != 0.0f;
-        if (nz) {
-          float* g0 = grad2d + (size_t)rr * 4;
-          float* g1 = g0 + VN * 4;
-          red_add4(g0, g[0], g[1], g[2], g[3]);
-          red_add4(g1, g[4], g[5], g[6], g[7]);
-          red_add(g1 + VN * 4, g[8]);
-        }
-      }
+      // ---- phase B: per hit, its sums over the block; 1, 2 or 4 lanes per hit by the group's size ----
+      const int hc = max(min(ghi, cnt) - glo, 0);
+      const int hmax = max(hc, min(ghi, other) - glo);  // warp-uniform
+      if (hmax <= 4)
+        phase_b<4>(W, wp.half, l16, hc, glo, my_idx, bx0, by0, VN, grad2d);
+      else if (hmax <= 8)
+        phase_b<2>(W, wp.half, l16, hc, glo, my_idx, bx0, by0, VN, grad2d);
+      else
+        phase_b<1>(W, wp.half, l16, hc, glo, my_idx, bx0, by0, VN, grad2d);
       __syncwarp();
     }
     __syncwarp();
