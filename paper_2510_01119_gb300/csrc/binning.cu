@@ -4,6 +4,8 @@
 // Every kernel reads the pair count from device memory (never from the host), so the whole
 // binning step can sit inside a captured CUDA graph; grids are sized for the capacity and blocks
 // beyond the live count return at once.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace i4d {
@@ -307,16 +309,37 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
 }
 
 // ---- tile ranges ------------------------------------------------------------------------------------------
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* __restrict__ n_dev,
-                                   int64_t capacity, uint32_t* __restrict__ ranges, int32_t* __restrict__ status) {
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ keys,
+                                                          const int64_t* __restrict__ n_dev, int64_t capacity,
+                                                          uint32_t* __restrict__ ranges, int32_t* __restrict__ status) {
   const int64_t total = *n_dev;
   const int64_t n = total < capacity ? total : capacity;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && total > capacity) set_status(status, I4D_ERR_CAPACITY);
-  if (i >= n) return;
-  const uint32_t t = keys[i];
-  if (i == 0 || keys[i - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)i;
-  if (i == n - 1 || keys[i + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && total > capacity) set_status(status, I4D_ERR_CAPACITY);
+  // four keys per thread (one 16-byte load), their neighbours one load each
+  const int64_t n4 = (n + 3) / 4;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * g;
+    uint32_t k[4];
+    if (i0 + 4 <= n) {
+      const uint4 v = reinterpret_cast<const uint4*>(keys)[g];
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = (i0 + j < n) ? keys[i0 + j] : 0u;
+    }
+    const uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0u;
+    const uint32_t next = i0 + 4 < n ? keys[i0 + 4] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= n) break;
+      const uint32_t t = k[j];
+      const uint32_t left = j ? k[j - 1] : prev;
+      const uint32_t right = j < 3 ? k[j + 1] : next;
+      if (i == 0 || left != t) ranges[2 * (int64_t)t] = (uint32_t)i;
+      if (i == n - 1 || right != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
+    }
+  }
 }
 
 // Tiles ordered by decreasing list length, in buckets of a quarter octave (order inside a bucket is
@@ -499,7 +522,7 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_dev, int64
   if (e != cudaSuccess) return e;
   I4D_PROF("tile_ranges", st);
   const int threads = 256;
-  const int64_t blocks = (capacity + threads - 1) / threads;
+  const int64_t blocks = std::min<int64_t>((capacity / 4 + threads) / threads, 152 * 16);
   tile_ranges_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), threads, 0, st>>>(keys, n_dev, capacity, ranges, status);
   {
     I4D_PROF("tile_order", st);
