@@ -5,7 +5,8 @@
 // C2 = 0.03^2.  The forward kernel stages a 42x26 halo tile of image and target in shared memory,
 // blurs the five products (x, y, x^2, y^2, x y) horizontally then vertically for a 32x16 output
 // tile, and writes per pixel the three partial derivatives of S with respect to the moments
-// (a = dS/dmu_x, b = dS/ds_xx, c = dS/ds_xy) plus block sums of S and |x - y|.  The backward kernel
+// (a = dS/dmu_x, b = dS/ds_xx, c = dS/ds_xy) plus block sums of S and |x - y| (FP32 within a block,
+// FP64 across blocks).  The backward kernel
 // blurs a, b, c the same way (the window is symmetric) and writes
 // dL/dx = ((1 - lambda) sign(x - y) - lambda (w*a + 2 x w*b + y w*c)) / count.
 #include <math.h>
@@ -44,13 +45,15 @@ __device__ __forceinline__ void decode(const ViewTable& vt, const SsimTiles& tt,
   ty = t / tt.tx[v];
 }
 
-__device__ __forceinline__ double block_sum_d(double x, double* red) {
+// Block sum by a shuffle tree (a block covers at most 512 pixels, so FP32 loses nothing that
+// matters; the totals over blocks accumulate in FP64).
+__device__ __forceinline__ float block_sum(float x, float* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = x;
   __syncthreads();
-  x = (threadIdx.x < kThreads / 32) ? red[lane] : 0.0;
+  x = (threadIdx.x < kThreads / 32) ? red[lane] : 0.0f;
   if (warp == 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -58,13 +61,21 @@ __device__ __forceinline__ double block_sum_d(double x, double* red) {
   return x;  // valid in thread 0
 }
 
+// Work split of the blur passes: the horizontal pass gives each of kHH x 8 threads four adjacent
+// outputs of a row (14 inputs in registers for 4 x 11 taps), the vertical pass gives each of the
+// 256 threads two vertically adjacent outputs of a column (12 inputs for 2 x 11 taps).
+constexpr int kHCols = 4;
+constexpr int kHItems = kHH * (kSW / kHCols);
+static_assert(kHItems <= kThreads, "one horizontal item per thread");
+static_assert(kSW * (kSH / 2) == kThreads, "one vertical pair per thread");
+
 __global__ void __launch_bounds__(kThreads) ssim_fwd_kernel(ViewTable vt, SsimTiles tt, const float* __restrict__ img,
                                                             const float* __restrict__ tgt, Win w,
                                                             float* __restrict__ abc, int64_t plane,
                                                             double* __restrict__ acc) {
   __shared__ float sx[kHH][kHW], sy[kHH][kHW];
   __shared__ float hs[5][kHH][kSW];
-  __shared__ double red[kThreads / 32];
+  __shared__ float red[kThreads / 32];
   int v, ch, tx, ty;
   decode(vt, tt, blockIdx.x, v, ch, tx, ty);
   const int W = vt.width[v], H = vt.height[v];
@@ -79,62 +90,81 @@ __global__ void __launch_bounds__(kThreads) ssim_fwd_kernel(ViewTable vt, SsimTi
     sy[r][c] = in ? tgt[o] : 0.0f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kHH * kSW; i += kThreads) {
-    const int r = i / kSW, c = i - r * kSW;
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+  if (threadIdx.x < kHItems) {
+    const int r = threadIdx.x / (kSW / kHCols), c0 = kHCols * (threadIdx.x % (kSW / kHCols));
+    float m[5][kHCols];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float x = sx[r][c + k], y = sy[r][c + k], g = w.g[k];
-      m0 = fmaf(g, x, m0);
-      m1 = fmaf(g, y, m1);
-      m2 = fmaf(g, x * x, m2);
-      m3 = fmaf(g, y * y, m3);
-      m4 = fmaf(g, x * y, m4);
+    for (int j = 0; j < kHCols; ++j) m[0][j] = m[1][j] = m[2][j] = m[3][j] = m[4][j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + kHCols; ++k) {
+      const float x = sx[r][c0 + k], y = sy[r][c0 + k];
+      const float xx = x * x, yy = y * y, xy = x * y;
+#pragma unroll
+      for (int j = 0; j < kHCols; ++j) {
+        if (k - j < 0 || k - j > 2 * kR) continue;
+        const float g = w.g[k - j];
+        m[0][j] = fmaf(g, x, m[0][j]);
+        m[1][j] = fmaf(g, y, m[1][j]);
+        m[2][j] = fmaf(g, xx, m[2][j]);
+        m[3][j] = fmaf(g, yy, m[3][j]);
+        m[4][j] = fmaf(g, xy, m[4][j]);
+      }
     }
-    hs[0][r][c] = m0;
-    hs[1][r][c] = m1;
-    hs[2][r][c] = m2;
-    hs[3][r][c] = m3;
-    hs[4][r][c] = m4;
+#pragma unroll
+    for (int j = 0; j < kHCols; ++j) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) hs[q][r][c0 + j] = m[q][j];
+    }
   }
   __syncthreads();
-  double s_sum = 0.0, l1_sum = 0.0;
-  for (int p = threadIdx.x; p < kSH * kSW; p += kThreads) {
-    const int r = p / kSW, c = p - r * kSW;
-    const int gy = ty * kSH + r, gx = tx * kSW + c;
-    if (gy >= H || gx >= W) continue;
-    float mx = 0.f, my = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
+  float s_sum = 0.0f, l1_sum = 0.0f;
+  {
+    const int c = threadIdx.x % kSW, r0 = 2 * (threadIdx.x / kSW);
+    float mo[2][5];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float g = w.g[k];
-      mx = fmaf(g, hs[0][r + k][c], mx);
-      my = fmaf(g, hs[1][r + k][c], my);
-      sxx = fmaf(g, hs[2][r + k][c], sxx);
-      syy = fmaf(g, hs[3][r + k][c], syy);
-      sxy = fmaf(g, hs[4][r + k][c], sxy);
+    for (int j = 0; j < 2; ++j) mo[j][0] = mo[j][1] = mo[j][2] = mo[j][3] = mo[j][4] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 2; ++k) {
+      float hv[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) hv[q] = hs[q][r0 + k][c];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (k - j < 0 || k - j > 2 * kR) continue;
+        const float g = w.g[k - j];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) mo[j][q] = fmaf(g, hv[q], mo[j][q]);
+      }
     }
-    const float vx = sxx - mx * mx, vy = syy - my * my, cov = sxy - mx * my;
-    const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * cov + kC2;
-    const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-    const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
-    const float S = A1 * A2 * iB1 * iB2;
-    // S as a function of (mu_x, s_xx, s_xy), mu_y and s_yy held fixed
-    const float da = 2.0f * my * (A2 - A1) * iB1 * iB2 - 2.0f * mx * S * (iB1 - iB2);
-    const float db = -S * iB2;
-    const float dc = 2.0f * A1 * iB1 * iB2;
-    const int64_t o = base + (int64_t)gy * W + gx;
-    abc[o] = da;
-    abc[plane + o] = db;
-    abc[2 * plane + o] = dc;
-    s_sum += (double)S;
-    l1_sum += (double)fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + j;
+      const int gy = ty * kSH + r, gx = tx * kSW + c;
+      if (gy >= H || gx >= W) continue;
+      const float mx = mo[j][0], my = mo[j][1], sxx = mo[j][2], syy = mo[j][3], sxy = mo[j][4];
+      const float vx = sxx - mx * mx, vy = syy - my * my, cov = sxy - mx * my;
+      const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * cov + kC2;
+      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+      const float iB1 = 1.0f / B1, iB2 = 1.0f / B2;
+      const float S = A1 * A2 * iB1 * iB2;
+      // S as a function of (mu_x, s_xx, s_xy), mu_y and s_yy held fixed
+      const float da = 2.0f * my * (A2 - A1) * iB1 * iB2 - 2.0f * mx * S * (iB1 - iB2);
+      const float db = -S * iB2;
+      const float dc = 2.0f * A1 * iB1 * iB2;
+      const int64_t o = base + (int64_t)gy * W + gx;
+      abc[o] = da;
+      abc[plane + o] = db;
+      abc[2 * plane + o] = dc;
+      s_sum += S;
+      l1_sum += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+    }
   }
-  s_sum = block_sum_d(s_sum, red);
+  s_sum = block_sum(s_sum, red);
   __syncthreads();
-  l1_sum = block_sum_d(l1_sum, red);
+  l1_sum = block_sum(l1_sum, red);
   if (threadIdx.x == 0) {
-    atomicAdd(&acc[0], s_sum);
-    atomicAdd(&acc[1], l1_sum);
+    atomicAdd(&acc[0], (double)s_sum);
+    atomicAdd(&acc[1], (double)l1_sum);
   }
 }
 
@@ -159,38 +189,58 @@ __global__ void __launch_bounds__(kThreads) ssim_bwd_kernel(ViewTable vt, SsimTi
     sa[2][r][c] = in ? abc[2 * plane + o] : 0.0f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kHH * kSW; i += kThreads) {
-    const int r = i / kSW, c = i - r * kSW;
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+  if (threadIdx.x < kHItems) {
+    const int r = threadIdx.x / (kSW / kHCols), c0 = kHCols * (threadIdx.x % (kSW / kHCols));
+    float m[3][kHCols];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float g = w.g[k];
-      m0 = fmaf(g, sa[0][r][c + k], m0);
-      m1 = fmaf(g, sa[1][r][c + k], m1);
-      m2 = fmaf(g, sa[2][r][c + k], m2);
+    for (int j = 0; j < kHCols; ++j) m[0][j] = m[1][j] = m[2][j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + kHCols; ++k) {
+      const float a0 = sa[0][r][c0 + k], a1 = sa[1][r][c0 + k], a2 = sa[2][r][c0 + k];
+#pragma unroll
+      for (int j = 0; j < kHCols; ++j) {
+        if (k - j < 0 || k - j > 2 * kR) continue;
+        const float g = w.g[k - j];
+        m[0][j] = fmaf(g, a0, m[0][j]);
+        m[1][j] = fmaf(g, a1, m[1][j]);
+        m[2][j] = fmaf(g, a2, m[2][j]);
+      }
     }
-    hs[0][r][c] = m0;
-    hs[1][r][c] = m1;
-    hs[2][r][c] = m2;
+#pragma unroll
+    for (int j = 0; j < kHCols; ++j) {
+      hs[0][r][c0 + j] = m[0][j];
+      hs[1][r][c0 + j] = m[1][j];
+      hs[2][r][c0 + j] = m[2][j];
+    }
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < kSH * kSW; p += kThreads) {
-    const int r = p / kSW, c = p - r * kSW;
-    const int gy = ty * kSH + r, gx = tx * kSW + c;
-    if (gy >= H || gx >= W) continue;
-    float ga = 0.f, gb = 0.f, gc = 0.f;
+  {
+    const int c = threadIdx.x % kSW, r0 = 2 * (threadIdx.x / kSW);
+    float go[2][3];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float g = w.g[k];
-      ga = fmaf(g, hs[0][r + k][c], ga);
-      gb = fmaf(g, hs[1][r + k][c], gb);
-      gc = fmaf(g, hs[2][r + k][c], gc);
+    for (int j = 0; j < 2; ++j) go[j][0] = go[j][1] = go[j][2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 2; ++k) {
+      const float h0 = hs[0][r0 + k][c], h1 = hs[1][r0 + k][c], h2 = hs[2][r0 + k][c];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (k - j < 0 || k - j > 2 * kR) continue;
+        const float g = w.g[k - j];
+        go[j][0] = fmaf(g, h0, go[j][0]);
+        go[j][1] = fmaf(g, h1, go[j][1]);
+        go[j][2] = fmaf(g, h2, go[j][2]);
+      }
     }
-    const int64_t o = base + (int64_t)gy * W + gx;
-    const float x = img[o], y = tgt[o], d = x - y;
-    const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-    const float dS = ga + 2.0f * x * gb + y * gc;
-    dimg[o] = ((1.0f - lam) * sgn - lam * dS) * inv_count;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gy = ty * kSH + r0 + j, gx = tx * kSW + c;
+      if (gy >= H || gx >= W) continue;
+      const int64_t o = base + (int64_t)gy * W + gx;
+      const float x = img[o], y = tgt[o], d = x - y;
+      const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+      const float dS = go[j][0] + 2.0f * x * go[j][1] + y * go[j][2];
+      dimg[o] = ((1.0f - lam) * sgn - lam * dS) * inv_count;
+    }
   }
 }
 
