@@ -84,23 +84,28 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load in, cons
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint64_t* __restrict__ bsum, int nb,
-                                                                int64_t* __restrict__ total) {
-  // nb <= kScanMaxBlocks = blockDim.x
-  const uint64_t x = threadIdx.x < nb ? bsum[threadIdx.x] : 0;
-  uint64_t ex;
-  const uint64_t tot = block_excl_scan(x, ex);
-  if (threadIdx.x < nb) bsum[threadIdx.x] = ex;
-  if (threadIdx.x == 0 && total) *total = (int64_t)tot;
-}
-
 template <class Load>
 __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(Load in, uint32_t* __restrict__ out,
                                                                  const int64_t* __restrict__ n_dev, int64_t n_max,
-                                                                 int64_t chunk, const uint64_t* __restrict__ bsum) {
+                                                                 int64_t chunk, const uint64_t* __restrict__ bsum,
+                                                                 int64_t* __restrict__ total_out) {
   const int64_t n = n_dev ? min(*n_dev, n_max) : n_max;
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(lo + chunk, n);
-  uint64_t carry = bsum[blockIdx.x];
+  uint64_t carry;
+  {
+    __shared__ uint64_t red[32];
+    uint64_t x = (threadIdx.x < blockIdx.x) ? bsum[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    x = red[threadIdx.x & 31];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    carry = x;
+    __syncthreads();
+  }
+  if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = (int64_t)(carry + bsum[blockIdx.x]);
   for (int64_t base = lo; base < hi; base += kScanTile) {
     uint32_t v[kScanItems];
     uint64_t s = 0;
@@ -146,30 +151,69 @@ __global__ void __launch_bounds__(256) visible_compact_kernel(int64_t VN, const 
 }
 
 // Every (tile, Gaussian) pair of the k-th depth-ordered record's rectangle, at offs[k]: key = global
-// tile index, value = Gaussian id.
+// tile index, value = Gaussian id.  A warp emits its 32 records' pairs together, 32 consecutive
+// outputs per round: each lane finds the record that owns its output by a binary search over the
+// warp's inclusive prefix of the records' pair counts, so long and short rectangles cost the same
+// and every store is coalesced.
 __global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                           const int64_t* __restrict__ R_dev,
                                                           const uint32_t* __restrict__ rec,
                                                           const uint32_t* __restrict__ offs, int64_t capacity,
                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t VN = (int64_t)vt.n_views * n;
+  const int64_t R = *R_dev;
+  const int lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= *R_dev) return;
-  const uint32_t r = rec[k];
-  const int v = (int)(r / (uint32_t)n);
-  const uint32_t id = r - (uint32_t)v * (uint32_t)n;
-  int x0, y0, x1, y1;
-  box_rect(proj[3 * VN + r], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
-  int64_t o = offs[k];
-  const uint32_t base = (uint32_t)vt.tile_off[v];
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
-      if (o < capacity) {
-        keys[o] = base + (uint32_t)(ty * vt.tiles_x[v] + tx);
-        vals[o] = id;
-      }
-      ++o;
+  if (k - lane >= R) return;  // the whole warp is past the last record
+  int cnt = 0, x0 = 0, y0 = 0, w = 1, txs = 0;
+  uint32_t id = 0, tbase = 0;
+  int64_t o = 0;
+  if (k < R) {
+    const uint32_t r = rec[k];
+    const int v = (int)(r / (uint32_t)n);
+    id = r - (uint32_t)v * (uint32_t)n;
+    int x1, y1;
+    box_rect(proj[3 * VN + r], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+    if (x1 > x0 && y1 > y0) {
+      w = x1 - x0;
+      cnt = w * (y1 - y0);
     }
+    o = offs[k];
+    tbase = (uint32_t)vt.tile_off[v];
+    txs = vt.tiles_x[v];
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int excl = incl - cnt;
+  for (int s0 = 0; s0 < total; s0 += 32) {  // warp-uniform
+    const int s = s0 + lane;
+    // owner: the number of lanes whose inclusive count is <= s (counts are nonnegative)
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int t = __shfl_sync(0xffffffffu, incl, j + step - 1);
+      if (t <= s) j += step;
+    }
+    const int loc = s - __shfl_sync(0xffffffffu, excl, j);
+    const int wj = __shfl_sync(0xffffffffu, w, j);
+    const int x0j = __shfl_sync(0xffffffffu, x0, j), y0j = __shfl_sync(0xffffffffu, y0, j);
+    const int txj = __shfl_sync(0xffffffffu, txs, j);
+    const uint32_t tbj = __shfl_sync(0xffffffffu, tbase, j), idj = __shfl_sync(0xffffffffu, id, j);
+    const int64_t oj = __shfl_sync(0xffffffffu, o, j);
+    if (s < total) {
+      const int dy = loc / wj, dx = loc - dy * wj;
+      const int64_t out = oj + loc;
+      if (out < capacity) {
+        keys[out] = tbj + (uint32_t)((y0j + dy) * txj + x0j + dx);
+        vals[out] = idj;
+      }
+    }
+  }
 }
 
 // ---- radix sort ---------------------------------------------------------------------------------------
@@ -392,8 +436,7 @@ cudaError_t scan_impl(Load in, uint32_t* out, int64_t n_max, const int64_t* n_de
   }
   I4D_PROF("scan", st);
   scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n_dev, n_max, chunk, bsum);
-  scan_top_kernel<<<1, kScanThreads, 0, st>>>(bsum, nb, total);
-  scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n_dev, n_max, chunk, bsum);
+  scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n_dev, n_max, chunk, bsum, total);
   return cudaGetLastError();
 }
 }  // namespace

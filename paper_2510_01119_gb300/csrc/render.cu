@@ -2,12 +2,13 @@
 //
 // One CTA per (view, tile), taken longest list first.  Each 16-lane half-warp owns an 8x4 pixel
 // block of the tile and each thread two vertically adjacent pixels, whose arithmetic runs side by
-// side on the packed FP32x2 instructions (one instruction per operation for both pixels).  The warps of a CTA never
-// synchronise with one another: each warp streams its tile's depth-sorted list in chunks of 32
-// entries, one entry per lane, tests the entry's ellipse box (precomputed by slice_project) against
-// the blocks of its two halves, and stages the hits of each half -- compacted in list order by a
-// ballot and a prefix count -- in that half's shared-memory slots; each half's pixels then visit
-// only those hits, the two halves side by side.  The test is exact: the box holds every pixel
+// side on the packed FP32x2 instructions (one instruction per operation for both pixels).  The
+// warps of a CTA never synchronise with one another: each warp streams its tile's depth-sorted list
+// in chunks of 32 entries, one entry per lane, tests the entry's ellipse box (precomputed by
+// slice_project) against the blocks of its two halves, and stages the hits of each half --
+// compacted in list order by a ballot and a prefix count -- in shared memory (the forward keeps a
+// copy per half, the backward stores each entry once with per-half index lists); each half's pixels
+// then visit only those hits, the two halves side by side.  The test is exact: the box holds every pixel
 // centre where the fragment can be blended (q <= q_max and alpha >= alpha_min).  A warp stops as
 // soon as all its pixels are saturated (forward) or when it has passed its pixels' last blended
 // fragments (backward).
