@@ -166,8 +166,15 @@ __device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st,
   return __popc(wp.half ? m1 : m0);
 }
 
+// Resident CTAs per SM the forward is compiled for: 36 warps, which caps the registers at 56 per
+// thread (the kernel needs 63 unbounded, which allows 32 warps).
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2) render_fwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
+constexpr int fwd_min_blocks() {
+  return (TW * TH / 64) >= 36 ? 1 : (36 / (TW * TH / 64) > 32 ? 32 : 36 / (TW * TH / 64));
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_fwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ ranges, Settings S,
                                                                  float* __restrict__ img, float* __restrict__ T_final,
