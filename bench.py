@@ -440,9 +440,9 @@ def run_configs(dev, wl, vid):
 def oracle_workload(vid):
     import oracle
     import synth
-    pts = np.concatenate([oracle.backproject(c, vid["depth"][f]) for f, c in enumerate(vid["cams"])]).astype(np.float32)
-    rgb = vid["rgb"].reshape(-1, 3).astype(np.float32) / 255.0
-    t = np.repeat(vid["times"], VIDEO_W * VIDEO_H).astype(np.float32)
+    pts = oracle.backproject_video_f32(vid)
+    rgb = vid["rgb"].reshape(-1, 3).astype(np.float32) / np.float32(255.0)
+    t = np.repeat(np.asarray(vid["times"], np.float32), VIDEO_W * VIDEO_H)
     t0 = time.perf_counter()
     res = oracle.prune(pts, synth.PRUNE_VOXEL, synth.PRUNE_VOXEL, synth.PRUNE_MIN_SUPPORT, rgb=rgb, t=t,
                        dyn=vid["dyn"].reshape(-1))

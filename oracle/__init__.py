@@ -30,7 +30,7 @@ MODE_FULL, MODE_ISO_ROT, MODE_ISO_IDENTITY = 0, 1, 2
 
 # projected-record columns (must follow the enum in i4d_oracle.c)
 PCOLS = ["visible", "u", "v", "depth", "ot", "ca", "cb", "cc", "radius", "r", "g", "b",
-         "x0", "y0", "x1", "y1", "margin", "rect_margin",
+         "margin", "radius_margin",
          "m3x", "m3y", "m3z", "s3xx", "s3xy", "s3xz", "s3yy", "s3yz", "s3zz"]
 P = {name: k for k, name in enumerate(PCOLS)}
 # 2D-gradient columns
@@ -57,7 +57,7 @@ def _load():
     global _lib
     if _lib is None:
         lib = ctypes.CDLL(build())
-        lib.orc_tile_pairs.restype = ctypes.c_long
+        lib.orc_tile_lists.restype = ctypes.c_long
         lib.orc_prune.restype = ctypes.c_long
         _lib = lib
     return _lib
@@ -117,15 +117,18 @@ def _sch_arrays(g: dict):
     return nt, _f64(np.asarray(g["sch"]).reshape(g["mean4"].shape[0], nt - 1, (int(g.get("sh_deg", 0)) + 1) ** 2, 3))
 
 
-def project(g: dict, cam: dict, tile=(16, 16), settings=None) -> np.ndarray:
-    """Eq. 7-8 slicing, temporal opacity, EWA projection and colour for every Gaussian -> (n, 27)."""
+def project(g: dict, cam: dict, settings=None) -> np.ndarray:
+    """Eq. 7-8 slicing, temporal opacity, EWA projection and colour for every Gaussian -> (n, 23).
+    visible = not culled (temporal opacity, near plane, degenerate 2D covariance); margin = the
+    smallest relative distance of those decisions from their thresholds; radius_margin = that of
+    the 3-sigma radius ceil(3 sqrt(lambda_max)) from an integer."""
     lib = _load()
     n, deg, mode, m4, ls4, ql, qr, op, rgb, sh = _gauss_arrays(g)
     S = settings if settings is not None else settings_array()
     out = np.zeros((n, len(PCOLS)), dtype=np.float64)
     nt, sch = _sch_arrays(g)
     rc = lib.orc_project(n, deg, mode, _ptr(m4), _ptr(ls4), _ptr(ql), _ptr(qr), _ptr(op), _ptr(rgb), _ptr(sh),
-                         nt, _ptr(sch), _ptr(camera_array(cam)), int(tile[0]), int(tile[1]), _ptr(S), _ptr(out))
+                         nt, _ptr(sch), _ptr(camera_array(cam)), _ptr(S), _ptr(out))
     if rc != 0:
         raise ValueError(f"orc_project failed ({rc})")
     return out
@@ -156,6 +159,25 @@ def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=N
     return (img, T, nc, mg, dmg) if depth_margin else (img, T, nc, mg)
 
 
+def render_orders(proj: np.ndarray, cam: dict, pix, depth_margin: float, max_alt: int = 64, bg=(0.0, 0.0, 0.0),
+                  settings=None):
+    """Every valid colour of each pixel in `pix` when fragments whose depths differ by less than
+    depth_margin (relative) may come in either order: (alt (npix, max_alt, 3), n_alt (npix,)), n_alt =
+    the number of orders (alt[:, 0] is the (depth, id) order), -1 when there are more than max_alt."""
+    lib = _load()
+    S = settings if settings is not None else settings_array()
+    pix_arr = np.ascontiguousarray(pix, dtype=np.int32)
+    npix = pix_arr.shape[0]
+    alt = np.zeros((npix, max_alt, 3), dtype=np.float64)
+    n_alt = np.zeros(npix, dtype=np.int32)
+    rc = lib.orc_render_orders(proj.shape[0], _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)),
+                               _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), ctypes.c_double(depth_margin),
+                               int(max_alt), _ptr(alt), _ptr(n_alt))
+    if rc != 0:
+        raise RuntimeError(f"orc_render_orders failed ({rc})")
+    return alt, n_alt
+
+
 def render_bwd(g: dict, cam: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), settings=None, pix=None):
     """Analytic backward for one camera -> (grad2d (n,9), dict of parameter gradients)."""
     lib = _load()
@@ -182,20 +204,29 @@ def render_bwd(g: dict, cam: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), sett
     return g2, grads
 
 
-def tile_pairs(proj: np.ndarray, cam: dict, tile=(16, 16), tile_offset: int = 0):
-    """(tile, id) pairs of the visible Gaussians' tile rectangles in (tile, depth, id) order."""
+def tile_lists(proj: np.ndarray, cam: dict, tile=(16, 16), tile_offset: int = 0, settings=None,
+               margin: float = 1e-4):
+    """Binning (Sec. 3.1): every (tile, Gaussian) pair whose tile holds a pixel centre where the
+    Gaussian can be blended (q <= q_max and o_t exp(-q/2) >= alpha_min), ordered by (tile, depth, id).
+    Returns (tiles, ids, status): status 1 = needed, 2 = only pixel centres within `margin` (relative)
+    of a threshold, so a float32 evaluation may take or drop the pair."""
     lib = _load()
-    tiles_x = (int(cam["W"]) + tile[0] - 1) // tile[0]
-    vis = proj[:, P["visible"]] != 0
-    area = ((proj[:, P["x1"]] - proj[:, P["x0"]]) * (proj[:, P["y1"]] - proj[:, P["y0"]]))[vis]
-    cap = int(area.sum())
-    tiles = np.zeros(max(cap, 1), dtype=np.int32)
-    ids = np.zeros(max(cap, 1), dtype=np.int32)
-    cnt = lib.orc_tile_pairs(proj.shape[0], _ptr(np.ascontiguousarray(proj)), tiles_x, int(tile_offset),
-                             ctypes.c_long(cap), _ptr(tiles), _ptr(ids))
-    if cnt < 0:
-        raise RuntimeError(f"orc_tile_pairs failed ({cnt})")
-    return tiles[:cnt], ids[:cnt]
+    S = settings if settings is not None else settings_array()
+    P = np.ascontiguousarray(proj)
+    cap = 1 << 16
+    while True:
+        tiles = np.zeros(cap, dtype=np.int32)
+        ids = np.zeros(cap, dtype=np.int32)
+        st = np.zeros(cap, dtype=np.int32)
+        cnt = lib.orc_tile_lists(P.shape[0], _ptr(P), _ptr(camera_array(cam)), int(tile[0]), int(tile[1]),
+                                 int(tile_offset), _ptr(S), ctypes.c_double(margin), ctypes.c_long(cap), _ptr(tiles),
+                                 _ptr(ids), _ptr(st))
+        if cnt == -1 and cap < (1 << 34):
+            cap *= 4
+            continue
+        if cnt < 0:
+            raise RuntimeError(f"orc_tile_lists failed ({cnt})")
+        return tiles[:cnt], ids[:cnt], st[:cnt]
 
 
 def backproject(cam: dict, depth: np.ndarray) -> np.ndarray:
@@ -205,6 +236,28 @@ def backproject(cam: dict, depth: np.ndarray) -> np.ndarray:
     assert W == int(cam["W"]) and H == int(cam["H"])
     out = np.zeros((H * W, 3), dtype=np.float64)
     lib.orc_backproject(_ptr(camera_array(cam)), _ptr(np.ascontiguousarray(depth, dtype=np.float32)), _ptr(out))
+    return out
+
+
+def backproject_f32(cam: dict, depth: np.ndarray) -> np.ndarray:
+    """Eq. 5 as a fixed sequence of correctly rounded float32 operations (camera rounded to float32
+    first) -> (H*W, 3) float32: the reading under which pruning the back-projected cloud is
+    bit-reproducible.  Pinned against the float64 form within its rounding-error bound."""
+    lib = _load()
+    H, W = depth.shape
+    assert W == int(cam["W"]) and H == int(cam["H"])
+    out = np.zeros((H * W, 3), dtype=np.float32)
+    lib.orc_backproject_f32(_ptr(camera_array(cam)), _ptr(np.ascontiguousarray(depth, dtype=np.float32)), _ptr(out))
+    return out
+
+
+def backproject_video_f32(vid: dict) -> np.ndarray:
+    """backproject_f32 of every frame of a depth video, frames concatenated (point index
+    f*H*W + py*W + px) -> (F*H*W, 3) float32."""
+    F, H, W = vid["depth"].shape
+    out = np.empty((F * H * W, 3), dtype=np.float32)
+    for f, c in enumerate(vid["cams"]):
+        out[f * H * W:(f + 1) * H * W] = backproject_f32(c, vid["depth"][f])
     return out
 
 

@@ -45,7 +45,7 @@ enum { C_R = 0, C_T = 9, C_FX = 12, C_FY, C_CX, C_CY, C_W, C_H, C_TIME, C_COUNT 
 /* projected record columns */
 enum {
   P_VISIBLE = 0, P_U, P_V, P_DEPTH, P_OT, P_CA, P_CB, P_CC, P_RADIUS, P_R, P_G, P_B,
-  P_X0, P_Y0, P_X1, P_Y1, P_MARGIN, P_RECT_MARGIN,
+  P_MARGIN, P_RADIUS_MARGIN,
   P_M3X, P_M3Y, P_M3Z, P_S3XX, P_S3XY, P_S3XZ, P_S3YY, P_S3YZ, P_S3ZZ, P_STRIDE
 };
 
@@ -171,8 +171,7 @@ typedef struct {
   double lam, radius, u, v;
   double dir[3], dirn, dhat[3], Y[15], dY[15][3], raw[3], rgb[3];
   int visible;
-  double margin, rect_margin;
-  int rect[4];
+  double margin, radius_margin;
 } gfwd;
 
 static double rel_margin(double x, double thr) { return fabs(x - thr) / fabs(thr); }
@@ -194,13 +193,12 @@ static int sch_stride(int deg, int nt) { return nt > 1 ? (nt - 1) * (deg + 1) * 
 
 static void forward_one(int i, int sh_deg, int mode, const double* mean4, const double* logscale4,
                         const double* ql, const double* qr, const double* opac, const double* rgb,
-                        const double* sh, int nt, const double* sch, const double* cam, int tile_w, int tile_h,
-                        const double* S, gfwd* f) {
+                        const double* sh, int nt, const double* sch, const double* cam, const double* S, gfwd* f) {
   memset(f, 0, sizeof(*f));
   const double* mu = mean4 + 4 * i;
   const double* ls = logscale4 + 4 * i;
   f->margin = INFINITY;
-  f->rect_margin = INFINITY;
+  f->radius_margin = INFINITY;
 
   /* scales and rotation (Sec. 3.3: diagonal scale, 4x4 rotation; isotropic variant ties xyz) */
   if (mode == MODE_FULL) {
@@ -308,7 +306,7 @@ static void forward_one(int i, int sh_deg, int mode, const double* mean4, const 
       f->lam = mid + sqrt(disc > 0.0 ? disc : 0.0);
       const double r3 = 3.0 * sqrt(f->lam);
       f->radius = ceil(r3);
-      f->rect_margin = fmin(f->rect_margin, frac_margin(r3) / fmax(r3, 1.0));
+      f->radius_margin = frac_margin(r3) / fmax(r3, 1.0);
     } else {
       vis = 0;
     }
@@ -341,38 +339,6 @@ static void forward_one(int i, int sh_deg, int mode, const double* mean4, const 
     }
   }
 
-  /*
-   * Tile rectangle.  A fragment is blended only where q <= q_max and alpha = o_t exp(-q/2) >=
-   * alpha_min, i.e. inside the ellipse q <= q_b = min(q_max, max(2 ln(o_t / alpha_min), 0) + 1e-3)
-   * (the 1e-3 keeps the bound conservative under rounding).  The blendable box holds that ellipse:
-   * half-widths sqrt(q_b Sigma2_xx) and sqrt(q_b Sigma2_yy) (the inverse conic's diagonal), widened
-   * by 1% + 0.01 px.  The rectangle [x0,x1) x [y0,y1) is the set of tiles holding a pixel centre
-   * p + 0.5 of the box, clipped to the view; an empty rectangle culls the Gaussian in this view.
-   * Outside the box no pixel can be blended, so the image is the one a 3-sigma square would give.
-   */
-  if (vis) {
-    const int tx = (int)((cam[C_W] + tile_w - 1) / tile_w), ty = (int)((cam[C_H] + tile_h - 1) / tile_h);
-    const double qa = 2.0 * log(f->ot / S[S_ALPHA_MIN]);
-    const double qb = fmin(S[S_Q_MAX], (qa > 0.0 ? qa : 0.0) + 1e-3);
-    const double cdet = f->conic[0] * f->conic[2] - f->conic[1] * f->conic[1];
-    const double hx = sqrt(qb * f->conic[2] / cdet) * 1.01 + 0.01;
-    const double hy = sqrt(qb * f->conic[0] / cdet) * 1.01 + 0.01;
-    const double ax0 = (f->u - hx + 0.5) / tile_w, ax1 = (f->u + hx - 0.5) / tile_w;
-    const double ay0 = (f->v - hy + 0.5) / tile_h, ay1 = (f->v + hy - 0.5) / tile_h;
-    double x0 = floor(ax0), x1 = floor(ax1) + 1.0, y0 = floor(ay0), y1 = floor(ay1) + 1.0;
-    x0 = fmin(fmax(x0, 0.0), tx); x1 = fmin(fmax(x1, 0.0), tx);
-    y0 = fmin(fmax(y0, 0.0), ty); y1 = fmin(fmax(y1, 0.0), ty);
-    if (x1 < x0) x1 = x0;
-    if (y1 < y0) y1 = y0;
-    f->rect[0] = (int)x0; f->rect[1] = (int)y0; f->rect[2] = (int)x1; f->rect[3] = (int)y1;
-    /* closeness of an edge to a tile boundary, relative to the edge's coordinate and to the FP32
-       uncertainty of the half-widths, which grows with the ellipse's condition number */
-    const double cond = f->lam * f->lam / f->det;
-    const double unc = (fmax(hx, hy) / fmin(tile_w, tile_h)) * cond * 1e-3;
-    double rm = fmin(fmin(frac_margin(ax0), frac_margin(ax1)), fmin(frac_margin(ay0), frac_margin(ay1)));
-    f->rect_margin = fmin(f->rect_margin, rm / (fmax(fmax(fabs(ax1), fabs(ay1)), 1.0) + unc));
-    if ((f->rect[2] - f->rect[0]) * (f->rect[3] - f->rect[1]) == 0) vis = 0;
-  }
   f->visible = vis;
 }
 
@@ -382,8 +348,7 @@ static void store_record(const gfwd* f, double* rec) {
   rec[P_CA] = f->conic[0]; rec[P_CB] = f->conic[1]; rec[P_CC] = f->conic[2];
   rec[P_RADIUS] = f->radius;
   rec[P_R] = f->rgb[0]; rec[P_G] = f->rgb[1]; rec[P_B] = f->rgb[2];
-  rec[P_X0] = f->rect[0]; rec[P_Y0] = f->rect[1]; rec[P_X1] = f->rect[2]; rec[P_Y1] = f->rect[3];
-  rec[P_MARGIN] = f->margin; rec[P_RECT_MARGIN] = f->rect_margin;
+  rec[P_MARGIN] = f->margin; rec[P_RADIUS_MARGIN] = f->radius_margin;
   rec[P_M3X] = f->mean3[0]; rec[P_M3Y] = f->mean3[1]; rec[P_M3Z] = f->mean3[2];
   rec[P_S3XX] = f->cov3[0][0]; rec[P_S3XY] = f->cov3[0][1]; rec[P_S3XZ] = f->cov3[0][2];
   rec[P_S3YY] = f->cov3[1][1]; rec[P_S3YZ] = f->cov3[1][2]; rec[P_S3ZZ] = f->cov3[2][2];
@@ -395,14 +360,13 @@ static void store_record(const gfwd* f, double* rec) {
  */
 int orc_project(int n, int sh_deg, int mode, const double* mean4, const double* logscale4,
                 const double* ql, const double* qr, const double* opac, const double* rgb,
-                const double* sh, int nt, const double* sch, const double* cam, int tile_w, int tile_h,
-                const double* S, double* out) {
-  if (n < 0 || sh_deg < 0 || sh_deg > 3 || mode < 0 || mode > 2 || tile_w <= 0 || tile_h <= 0) return -1;
+                const double* sh, int nt, const double* sch, const double* cam, const double* S, double* out) {
+  if (n < 0 || sh_deg < 0 || sh_deg > 3 || mode < 0 || mode > 2) return -1;
   if (nt > 1 && !sch) return -1;
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     gfwd f;
-    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, tile_w, tile_h, S, &f);
+    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, S, &f);
     store_record(&f, out + (size_t)i * P_STRIDE);
   }
   return 0;
@@ -575,6 +539,95 @@ int orc_render(int n, const double* P, const double* cam, const double* bg, cons
       dmargin[j] = dmg;
     }
     free(buf);
+  }
+  return err;
+}
+
+/*
+ * Fragments whose depths differ by less than depth_margin (relative) have no order a float32
+ * pipeline can be held to: either order is a valid result of the (depth, id) sort.  For each pixel,
+ * group the blended candidates into maximal runs of consecutive fragments (in (depth, id) order)
+ * whose successive gaps are below depth_margin, and composite every order obtained by permuting
+ * within the runs.  alt: npix x max_alt x 3 colours (the first is the (depth, id) order itself);
+ * n_alt[j]: the number written, or -1 when the runs admit more than max_alt orders (alt then holds
+ * only the first).
+ */
+static int factorial(int g) { int f = 1; for (int k = 2; k <= g; ++k) f *= k; return f; }
+
+/* the idx-th permutation of 0..g-1 in lexicographic order (Lehmer code) */
+static void nth_permutation(int g, int idx, int* perm) {
+  int pool[8];
+  for (int k = 0; k < g; ++k) pool[k] = k;
+  for (int k = 0; k < g; ++k) {
+    const int f = factorial(g - 1 - k);
+    const int sel = idx / f;
+    idx %= f;
+    perm[k] = pool[sel];
+    for (int m = sel; m < g - 1 - k; ++m) pool[m] = pool[m + 1];
+  }
+}
+
+int orc_render_orders(int n, const double* P, const double* cam, const double* bg, const double* S, int npix,
+                      const int* pix, double depth_margin, int max_alt, double* alt, int* n_alt) {
+  const int W = (int)cam[C_W], H = (int)cam[C_H];
+  if ((pix == NULL && npix != W * H) || max_alt < 1) return -1;
+  int err = 0;
+#pragma omp parallel
+  {
+    frag* buf = (frag*)malloc(sizeof(frag) * (size_t)(n > 0 ? n : 1));
+    frag* tmp = (frag*)malloc(sizeof(frag) * (size_t)(n > 0 ? n : 1));
+    int* run_start = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int* run_len = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!buf || !tmp || !run_start || !run_len) {
+#pragma omp atomic write
+      err = -2;
+    }
+#pragma omp for schedule(dynamic, 16)
+    for (int j = 0; j < npix; ++j) {
+      if (err) continue;
+      const int p = pix ? pix[j] : j;
+      int cnt = compact_kept(buf, gather_pixel(n, P, S, p % W, p / W, buf));
+      /* runs of near-equal depth (only those of two or more fragments are permuted) */
+      int nruns = 0;
+      long orders = 1;
+      for (int k = 0; k < cnt;) {
+        int e = k + 1;
+        while (e < cnt && fabs(buf[e].depth - buf[e - 1].depth) < depth_margin * fabs(buf[e - 1].depth)) ++e;
+        if (e - k > 1) {
+          run_start[nruns] = k;
+          run_len[nruns] = e - k;
+          orders = (e - k > 7 || orders > max_alt) ? (long)max_alt + 1 : orders * factorial(e - k);
+          ++nruns;
+        }
+        k = e;
+      }
+      double C[3], T;
+      double* out = alt + (size_t)j * max_alt * 3;
+      composite(P, S, buf, cnt, bg, C, &T);
+      for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch];
+      if (orders > max_alt) {
+        n_alt[j] = -1;
+        continue;
+      }
+      for (long o = 1; o < orders; ++o) {
+        memcpy(tmp, buf, sizeof(frag) * (size_t)cnt);
+        long rem = o;
+        for (int r = 0; r < nruns; ++r) {
+          const int g = run_len[r], f = factorial(g);
+          int perm[8];
+          nth_permutation(g, (int)(rem % f), perm);
+          rem /= f;
+          for (int k = 0; k < g; ++k) tmp[run_start[r] + k] = buf[run_start[r] + perm[k]];
+        }
+        composite(P, S, tmp, cnt, bg, C, &T);
+        for (int ch = 0; ch < 3; ++ch) out[3 * o + ch] = C[ch];
+      }
+      n_alt[j] = (int)orders;
+    }
+    free(buf);
+    free(tmp);
+    free(run_start);
+    free(run_len);
   }
   return err;
 }
@@ -816,7 +869,7 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
   if (pix == NULL && npix != W * H) return -1;
   double* P = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * P_STRIDE);
   if (!P) return -2;
-  if (orc_project(n, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, 16, 16, S, P) != 0) {
+  if (orc_project(n, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, S, P) != 0) {
     free(P);
     return -1;
   }
@@ -864,7 +917,7 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
     for (int k = 0; k < G_STRIDE; ++k) any |= (g2[k] != 0.0);
     if (!any) continue;
     gfwd f;
-    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, 16, 16, S, &f);
+    forward_one(i, sh_deg, mode, mean4, logscale4, ql, qr, opac, rgb, sh, nt, sch, cam, S, &f);
     chain_to_params(i, sh_deg, mode, sh, nt, sch, cam, &f, g2, g_mean4, g_logscale4, g_ql, g_qr, g_opac, g_rgb,
                     g_sh, g_sch);
   }
@@ -875,7 +928,7 @@ int orc_render_bwd(int n, int sh_deg, int mode, const double* mean4, const doubl
 /* ------------------------------------------------------------------------------------------ */
 /* Tile lists (the (tile, depth, id) order of the binning step)                                 */
 /* ------------------------------------------------------------------------------------------ */
-typedef struct { int tile; double depth; int id; } tentry;
+typedef struct { int tile; double depth; int id; int status; } tentry;
 
 static int tentry_cmp(const void* pa, const void* pb) {
   const tentry* a = (const tentry*)pa;
@@ -887,36 +940,133 @@ static int tentry_cmp(const void* pa, const void* pb) {
 }
 
 /*
- * Every (tile, Gaussian) pair of the visible Gaussians' tile rectangles, ordered by
- * (tile, depth, id); tile = tile_offset + ty * tiles_x + tx.  Returns the pair count or -1
- * if it exceeds capacity (out_tile/out_id untouched beyond capacity).
+ * Tiles of one Gaussian that hold a blendable pixel centre.  By the coverage rule of the
+ * compositing, the Gaussian takes part at pixel centre p = (px + 0.5, py + 0.5) only where
+ * q(p) = (p - uv)^T conic (p - uv) <= q_max and alpha = o_t exp(-q/2) >= alpha_min, so a tile must
+ * list it exactly when one of its pixel centres (inside the view) satisfies both.  Every pixel
+ * centre of the box of the ellipse q <= q_max (half-widths sqrt(q_max Sigma2_xx), sqrt(q_max
+ * Sigma2_yy), Sigma2 the inverse conic) is tested, so none is missed.  Status per tile: 1 when a
+ * pixel centre passes both tests with relative slack above `margin`, 2 when no pixel does but one
+ * lies within `margin` of a threshold (a float32 evaluation may take or drop the tile), no entry
+ * otherwise.  Calls emit(tile index ty * tiles_x + tx, status) in row-major tile order.
  */
-long orc_tile_pairs(int n, const double* P, int tiles_x, int tile_offset, long capacity, int* out_tile, int* out_id) {
-  long total = 0;
-  for (int i = 0; i < n; ++i) {
-    const double* r = P + (size_t)i * P_STRIDE;
-    if (r[P_VISIBLE] == 0.0) continue;
-    total += (long)(r[P_X1] - r[P_X0]) * (long)(r[P_Y1] - r[P_Y0]);
-  }
-  if (total > capacity) return -1;
-  tentry* e = (tentry*)malloc(sizeof(tentry) * (size_t)(total > 0 ? total : 1));
-  if (!e) return -2;
-  long k = 0;
-  for (int i = 0; i < n; ++i) {
-    const double* r = P + (size_t)i * P_STRIDE;
-    if (r[P_VISIBLE] == 0.0) continue;
-    for (int ty = (int)r[P_Y0]; ty < (int)r[P_Y1]; ++ty)
-      for (int tx = (int)r[P_X0]; tx < (int)r[P_X1]; ++tx) {
-        e[k].tile = tile_offset + ty * tiles_x + tx;
-        e[k].depth = r[P_DEPTH];
-        e[k].id = i;
-        ++k;
+typedef void (*tile_sink)(void* ctx, int tile, int status);
+
+static void gaussian_tiles(const double* r, int W, int H, int tile_w, int tile_h, const double* S, double margin,
+                           int* scratch, tile_sink emit, void* ctx) {
+  const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
+  const double u = r[P_U], v = r[P_V], ca = r[P_CA], cb = r[P_CB], cc = r[P_CC], ot = r[P_OT];
+  const double det = ca * cc - cb * cb;
+  if (!(det > 0.0)) return;
+  const double qm = S[S_Q_MAX] * (1.0 + 2.0 * margin);
+  const double hx = sqrt(qm * cc / det) + 1.0, hy = sqrt(qm * ca / det) + 1.0;
+  int px0 = (int)floor(u - hx), px1 = (int)ceil(u + hx), py0 = (int)floor(v - hy), py1 = (int)ceil(v + hy);
+  if (px0 < 0) px0 = 0;
+  if (py0 < 0) py0 = 0;
+  if (px1 > W - 1) px1 = W - 1;
+  if (py1 > H - 1) py1 = H - 1;
+  if (px0 > px1 || py0 > py1) return;
+  const int tx0 = px0 / tile_w, tx1 = px1 / tile_w, ty0 = py0 / tile_h, ty1 = py1 / tile_h;
+  const int ntx = tx1 - tx0 + 1;
+  for (int k = 0; k < ntx * (ty1 - ty0 + 1); ++k) scratch[k] = 0;
+  for (int py = py0; py <= py1; ++py)
+    for (int px = px0; px <= px1; ++px) {
+      const double dx = px + 0.5 - u, dy = py + 0.5 - v;
+      const double q = ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy;
+      const double alpha = ot * exp(-0.5 * q);
+      const int blend = q <= S[S_Q_MAX] && alpha >= S[S_ALPHA_MIN];
+      const int near = rel_margin(q, S[S_Q_MAX]) < margin || rel_margin(alpha, S[S_ALPHA_MIN]) < margin;
+      int* st = &scratch[(py / tile_h - ty0) * ntx + (px / tile_w - tx0)];
+      if (blend && !near) *st = 1;
+      else if (near && *st == 0) *st = 2;
+    }
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      const int st = scratch[(ty - ty0) * ntx + (tx - tx0)];
+      if (st) emit(ctx, ty * tiles_x + tx, st);
+    }
+  (void)tiles_y;
+}
+
+typedef struct { long count; tentry* out; int id, tile_offset; double depth; } tile_ctx;
+
+static void count_sink(void* c, int tile, int status) {
+  (void)tile; (void)status;
+  ((tile_ctx*)c)->count++;
+}
+
+static void store_sink(void* c, int tile, int status) {
+  tile_ctx* t = (tile_ctx*)c;
+  tentry* e = &t->out[t->count++];
+  e->tile = t->tile_offset + tile;
+  e->depth = t->depth;
+  e->id = t->id;
+  e->status = status;
+}
+
+/*
+ * The tile lists of one view (the binning step of the 3D splatting renderer, Sec. 3.1): every
+ * (tile, Gaussian) pair of the visible Gaussians whose tile holds a blendable pixel centre (see
+ * gaussian_tiles), ordered by (tile, depth, id); tile = tile_offset + ty * tiles_x + tx.  Writes the
+ * pair's status (1 needed, 2 near a threshold) to out_status.  Returns the pair count, -1 if it
+ * exceeds capacity, -2 on allocation failure.
+ */
+long orc_tile_lists(int n, const double* P, const double* cam, int tile_w, int tile_h, int tile_offset,
+                    const double* S, double margin, long capacity, int* out_tile, int* out_id, int* out_status) {
+  const int W = (int)cam[C_W], H = (int)cam[C_H];
+  if (tile_w <= 0 || tile_h <= 0 || W <= 0 || H <= 0) return -3;
+  const int max_tiles = ((W + tile_w - 1) / tile_w + 1) * ((H + tile_h - 1) / tile_h + 1);
+  long* cnt = (long*)calloc((size_t)(n > 0 ? n : 1) + 1, sizeof(long));
+  if (!cnt) return -2;
+  int err = 0;
+#pragma omp parallel
+  {
+    int* scratch = (int*)malloc(sizeof(int) * (size_t)max_tiles);
+    if (!scratch) {
+#pragma omp atomic write
+      err = 1;
+    } else {
+#pragma omp for schedule(dynamic, 256)
+      for (int i = 0; i < n; ++i) {
+        const double* r = P + (size_t)i * P_STRIDE;
+        if (r[P_VISIBLE] == 0.0) continue;
+        tile_ctx c = {0, NULL, i, tile_offset, r[P_DEPTH]};
+        gaussian_tiles(r, W, H, tile_w, tile_h, S, margin, scratch, count_sink, &c);
+        cnt[i + 1] = c.count;
       }
+      free(scratch);
+    }
   }
-  qsort(e, total, sizeof(tentry), tentry_cmp);
+  if (err) { free(cnt); return -2; }
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  const long total = cnt[n > 0 ? n : 0];
+  if (total > capacity) { free(cnt); return -1; }
+  tentry* e = (tentry*)malloc(sizeof(tentry) * (size_t)(total > 0 ? total : 1));
+  if (!e) { free(cnt); return -2; }
+#pragma omp parallel
+  {
+    int* scratch = (int*)malloc(sizeof(int) * (size_t)max_tiles);
+    if (!scratch) {
+#pragma omp atomic write
+      err = 1;
+    } else {
+#pragma omp for schedule(dynamic, 256)
+      for (int i = 0; i < n; ++i) {
+        const double* r = P + (size_t)i * P_STRIDE;
+        if (r[P_VISIBLE] == 0.0 || cnt[i + 1] == cnt[i]) continue;
+        tile_ctx c = {0, e + cnt[i], i, tile_offset, r[P_DEPTH]};
+        gaussian_tiles(r, W, H, tile_w, tile_h, S, margin, scratch, store_sink, &c);
+      }
+      free(scratch);
+    }
+  }
+  free(cnt);
+  if (err) { free(e); return -2; }
+  qsort(e, (size_t)total, sizeof(tentry), tentry_cmp);
   for (long j = 0; j < total; ++j) {
     out_tile[j] = e[j].tile;
     out_id[j] = e[j].id;
+    out_status[j] = e[j].status;
   }
   free(e);
   return total;
@@ -941,6 +1091,48 @@ void orc_backproject(const double* cam, const float* depth, double* xyz) {
       double* out = xyz + 3 * ((size_t)py * W + px);
       for (int a = 0; a < 3; ++a)
         out[a] = cam[C_R + 0 * 3 + a] * d[0] + cam[C_R + 1 * 3 + a] * d[1] + cam[C_R + 2 * 3 + a] * d[2];
+    }
+}
+
+/*
+ * The same Eq. 5 as a fixed sequence of correctly rounded float32 operations, the reading under
+ * which the back-projected cloud (and so the voxel keys of the grid pruning) is bit-reproducible
+ * on any IEEE-754 machine.  The camera is first rounded to float32.  Per pixel, every line one
+ * rounding, evaluated in exactly this order and never contracted into a fused multiply-add:
+ *   u_x = px + 0.5                      (exact)
+ *   a_x = u_x - c_x                     n_x = a_x / f_x          X_c,x = D * n_x
+ *   (the same for y with c_y, f_y)      X_c,z = D
+ *   d_j = X_c,j - tau_j                 (j = x, y, z)
+ *   X_a = (W_xa d_x + W_ya d_y) + W_za d_z   (two products, their sum, the third product, the sum)
+ * depth: H x W float32; xyz out: H*W x 3 float32.
+ */
+void orc_backproject_f32(const double* cam, const float* depth, float* xyz) {
+  const int W = (int)cam[C_W], H = (int)cam[C_H];
+  float R[9], tau[3];
+  for (int k = 0; k < 9; ++k) R[k] = (float)cam[C_R + k];
+  for (int k = 0; k < 3; ++k) tau[k] = (float)cam[C_T + k];
+  const float fx = (float)cam[C_FX], fy = (float)cam[C_FY], cx = (float)cam[C_CX], cy = (float)cam[C_CY];
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const float D = depth[(size_t)py * W + px];
+      volatile float ux = (float)px + 0.5f, uy = (float)py + 0.5f;
+      volatile float ax = ux - cx, ay = uy - cy;
+      volatile float nx = ax / fx, ny = ay / fy;
+      volatile float xc[3];
+      xc[0] = D * nx;
+      xc[1] = D * ny;
+      xc[2] = D;
+      volatile float d[3];
+      for (int a = 0; a < 3; ++a) d[a] = xc[a] - tau[a];
+      float* out = xyz + 3 * ((size_t)py * W + px);
+      for (int a = 0; a < 3; ++a) {
+        volatile float p0 = R[0 * 3 + a] * d[0];
+        volatile float p1 = R[1 * 3 + a] * d[1];
+        volatile float s01 = p0 + p1;
+        volatile float p2 = R[2 * 3 + a] * d[2];
+        volatile float s = s01 + p2;
+        out[a] = s;
+      }
     }
 }
 
@@ -1047,7 +1239,7 @@ void orc_cov4(int mode, const double* logscale4, const double* ql, const double*
   const double cam[C_COUNT] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 5, 1, 1, 0, 0, 1, 1, 0};
   const double S[S_COUNT] = {0.99, 1.0 / 255.0, 1e-4, 9.0, 1.0 / 255.0, 0.2, 0.3, 1.3};
   gfwd f;
-  forward_one(0, 0, mode, mean4, logscale4, ql, qr, &opac, rgb, sh, 0, NULL, cam, 16, 16, S, &f);
+  forward_one(0, 0, mode, mean4, logscale4, ql, qr, &opac, rgb, sh, 0, NULL, cam, S, &f);
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) Sigma[4 * a + b] = f.Sig[a][b];
 }

@@ -218,3 +218,80 @@ def init_weights(seed: int) -> np.ndarray:
     w[off + 4] = 1.0
     w[off + 8] = 1.0
     return w
+
+
+def rotation_batch(ql, qr) -> np.ndarray:
+    """rotation() of many quaternion pairs at once -> (n, 4, 4): L(q_l / |q_l|) Rr(q_r / |q_r|)."""
+    ql = np.asarray(ql, np.float64)
+    qr = np.asarray(qr, np.float64)
+    a, b, c, d = (ql / np.linalg.norm(ql, axis=1, keepdims=True)).T
+    e, f, g, h = (qr / np.linalg.norm(qr, axis=1, keepdims=True)).T
+    L = np.stack([np.stack([a, -d, c, b], -1), np.stack([d, a, -b, c], -1),
+                  np.stack([-c, b, a, d], -1), np.stack([-b, -c, -d, a], -1)], 1)
+    M = np.stack([np.stack([e, h, -g, f], -1), np.stack([-h, e, f, g], -1),
+                  np.stack([g, -f, e, h], -1), np.stack([-f, -g, -h, e], -1)], 1)
+    return L @ M
+
+
+def motion_targets(g: dict) -> np.ndarray:
+    """Per Gaussian (n, 20): (log s_t, velocity v = b / c, R row-major), the values the learned
+    initialisation is trained to propose.  Sigma = R diag(s^2) R^T (Sec. 3.3) partitioned as
+    [[A, b], [b^T, c]]; by Eq. 7 the conditional mean moves as mu_xyz + b (t - mu_t) / c, so b / c is
+    the Gaussian's velocity.  ISO modes tie s_x = s_y = s_z to the first log-scale; ISO_IDENTITY
+    fixes R = I."""
+    ls = np.asarray(g["logscale4"], np.float64)
+    n = ls.shape[0]
+    mode = int(g.get("mode", 0))
+    s = np.exp(ls)
+    if mode != 0:
+        s[:, 1] = s[:, 2] = s[:, 0]
+    if mode == 2:
+        R = np.broadcast_to(np.eye(4), (n, 4, 4)).copy()
+    else:
+        R = rotation_batch(g["ql"], g["qr"])
+    Sig = np.einsum("nik,nk,njk->nij", R, s * s, R)
+    out = np.zeros((n, 20))
+    out[:, 0] = ls[:, 3]
+    out[:, 1:4] = Sig[:, 0:3, 3] / Sig[:, 3, 3][:, None]
+    out[:, 4:20] = R.reshape(n, 16)
+    return out
+
+
+def proposal_ok(y: np.ndarray) -> np.ndarray:
+    """The learned proposal y = (log s_t, v, q_l, q_r) of a point is used only when every value is
+    finite, both quaternions have squared norm above 1e-8 and -20 < log s_t < 5; otherwise the point
+    falls back to the heuristic.  Decided on the float32 values, in float32."""
+    y = np.asarray(y, np.float32)
+    fin = np.all(np.isfinite(y), axis=1)
+    with np.errstate(over="ignore", invalid="ignore"):
+        nl = np.sum(y[:, 4:8] * y[:, 4:8], axis=1, dtype=np.float32)
+        nr = np.sum(y[:, 8:12] * y[:, 8:12], axis=1, dtype=np.float32)
+    return fin & (nl > np.float32(1e-8)) & (nr > np.float32(1e-8)) & (y[:, 0] > -20) & (y[:, 0] < 5)
+
+
+def init_learned(pruned: dict, spatial, mlp_out, st_dynamic: float, st_static: float = 1.0,
+                 opacity: float = 0.1):
+    """4D Gaussians from pruned voxels with a per-point spatial scale and, where the proposal passes
+    proposal_ok(), the proposed temporal log-scale and quaternions; every other point takes the
+    heuristic of Sec. 4.1 (s_t by the dynamic flag, q_l = q_r = 1).  mlp_out None: the heuristic for
+    every point.  Returns (gaussians dict, number of fallbacks)."""
+    n = len(pruned["rep"])
+    mean4 = np.c_[np.asarray(pruned["centroid"], np.float64), np.asarray(pruned["t"], np.float64)]
+    ls = np.zeros((n, 4))
+    ls[:, :3] = np.log(np.asarray(spatial, np.float64)).reshape(-1, 1)
+    ls[:, 3] = np.where(np.asarray(pruned["flag"]) != 0, math.log(st_dynamic), math.log(st_static))
+    ql = np.zeros((n, 4))
+    ql[:, 0] = 1.0
+    qr = ql.copy()
+    fallbacks = 0
+    if mlp_out is not None:
+        y = np.asarray(mlp_out, np.float32)
+        ok = proposal_ok(y)
+        fallbacks = int((~ok).sum())
+        ls[ok, 3] = y[ok, 0]
+        ql[ok] = y[ok, 4:8]
+        qr[ok] = y[ok, 8:12]
+    g = dict(mean4=mean4, logscale4=ls, ql=ql, qr=qr,
+             opacity=np.full(n, math.log(opacity / (1.0 - opacity))),
+             rgb=np.asarray(pruned["rgb"], np.float64), sh=np.zeros((n, 0, 3)), sh_deg=0, mode=0)
+    return g, fallbacks

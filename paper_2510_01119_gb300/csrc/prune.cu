@@ -139,13 +139,15 @@ __global__ void __launch_bounds__(256) insert_depth_kernel(const float* __restri
     const int64_t pi = ((int64_t)f * H + py) * W + px;
     idx = (uint32_t)pi;
     const float D = depth[pi];
-    // Eq. 5: camera-space point D K^-1 (px + 0.5, py + 0.5, 1), world point R^T (X_c - t)
-    const float xc = D * (((float)px + 0.5f - c.cx) / c.fx);
-    const float yc = D * (((float)py + 0.5f - c.cy) / c.fy);
-    const float dx = xc - c.t[0], dy = yc - c.t[1], dz = D - c.t[2];
-    const float x = c.R[0] * dx + c.R[3] * dy + c.R[6] * dz;
-    const float y = c.R[1] * dx + c.R[4] * dy + c.R[7] * dz;
-    const float z = c.R[2] * dx + c.R[5] * dy + c.R[8] * dz;
+    // Eq. 5: camera-space point D K^-1 (px + 0.5, py + 0.5, 1), world point R^T (X_c - t), as a
+    // fixed sequence of correctly rounded float32 operations (no FMA contraction), so that every
+    // IEEE-754 machine computes the same cloud and hence the same voxel keys
+    const float xc = __fmul_rn(D, __fdiv_rn(__fsub_rn((float)px + 0.5f, c.cx), c.fx));
+    const float yc = __fmul_rn(D, __fdiv_rn(__fsub_rn((float)py + 0.5f, c.cy), c.fy));
+    const float dx = __fsub_rn(xc, c.t[0]), dy = __fsub_rn(yc, c.t[1]), dz = __fsub_rn(D, c.t[2]);
+    const float x = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], dx), __fmul_rn(c.R[3], dy)), __fmul_rn(c.R[6], dz));
+    const float y = __fadd_rn(__fadd_rn(__fmul_rn(c.R[1], dx), __fmul_rn(c.R[4], dy)), __fmul_rn(c.R[7], dz));
+    const float z = __fadd_rn(__fadd_rn(__fmul_rn(c.R[2], dx), __fmul_rn(c.R[5], dy)), __fmul_rn(c.R[8], dz));
     const int flag = dyn ? (dyn[pi] != 0) : 0;
     if (flag && inv_d == 0.0f) {
       key = unpruned_key(idx);

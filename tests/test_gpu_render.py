@@ -4,8 +4,8 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import (FLAG_MARGIN, GRAD_TOL, IMG_TOL, compare_images, oracle_views, rel_l2,
-                      suspicious_gaussians, tile_pairs_oracle)
+from gpu_util import (FLAG_MARGIN, GRAD_TOL, IMG_TOL, check_tile_lists, compare_images, flagged_gaussians,
+                      oracle_views, rel_l2, tile_lists_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -70,12 +70,17 @@ def test_slice_project_records_match_oracle(dev, orc, mode, deg):
     P = orc.project(g, cam)
     C = orc.P
     vis = P[:, C["visible"]] != 0
-    sus = suspicious_gaussians(orc, [P])[0]
+    sus = flagged_gaussians(orc, [P])[0]
     ok = np.array([i not in sus for i in range(n)])
-    # visibility and tile counts agree except at flagged decisions
-    area = (P[:, C["x1"]] - P[:, C["x0"]]) * (P[:, C["y1"]] - P[:, C["y0"]])
-    want_touched = np.where(vis, area, 0)
-    assert np.array_equal(touched[ok], want_touched[ok])
+    # a Gaussian with a tile that holds a blendable pixel centre is binned, on at least that many
+    # tiles; one the oracle culls is not binned (decisions within FLAG_MARGIN excepted)
+    wt, wi, ws = orc.tile_lists(P, cam)
+    need = np.bincount(wi[ws == 1], minlength=n)
+    assert np.all(touched[ok] >= need[ok])
+    assert np.all(touched[ok & ~vis] == 0)
+    print(f"records: {int(ok.sum())} compared, {int((~ok).sum())} flagged")
+    assert (~ok).sum() < 0.01 * n
+    vis = vis & (touched > 0)
     m = vis & ok
     assert m.sum() > 500
     u, v, ca, cb = planes[0, m].T
@@ -93,28 +98,20 @@ def test_slice_project_records_match_oracle(dev, orc, mode, deg):
     assert np.array_equal(radius, P[m, C["radius"]])
 
 
-def test_tile_lists_match_oracle_exactly(dev, orc):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_tile_lists_match_oracle(dev, orc, tile):
+    """The sorted (tile, id) list against the oracle's binning: every tile holding a blendable pixel
+    centre listed, every other listed tile within the documented slack of the blendable box, no
+    duplicate, depth order inside each tile (near-equal depths in either order)."""
     g = synth.gaussians_uniform(0)
     cams = [synth.camera(128, 96, 60.0, time=0.5), synth.camera(75, 41, 55.0, time=0.3)]
-    rast, _, _ = _gpu_render(g, cams)
+    rast, _, _ = _gpu_render(g, cams, tile=tile)
     tiles, ids = rast.tile_lists()
     Ps = [orc.project(g, c) for c in cams]
-    wt, wi = tile_pairs_oracle(orc, Ps, cams)
-    if len(tiles) == len(wt) and np.array_equal(tiles, wt) and np.array_equal(ids, wi):
-        return
-    # only pairs of flagged Gaussians may differ
-    sus = suspicious_gaussians(orc, Ps)
-    n0 = cams[0]["W"]
-    tiles_per_view0 = ((128 + 15) // 16) * ((96 + 15) // 16)
-
-    def keep(t, i):
-        v = 0 if t < tiles_per_view0 else 1
-        return i not in sus[v]
-
-    a = [(t, i) for t, i in zip(tiles, ids) if keep(t, i)]
-    b = [(t, i) for t, i in zip(wt, wi) if keep(t, i)]
-    assert a == b
-    assert sum(len(s) for s in sus) < 20, n0
+    rep = check_tile_lists(orc, tiles, ids, Ps, cams, tile)
+    print("tile lists:", rep)
+    assert rep["flagged_needed_pairs"] < 0.01 * rep["needed"]
+    assert rep["gpu"] <= 1.5 * rep["needed"]
 
 
 @pytest.mark.parametrize("mode,deg", [(0, 0), (1, 0), (2, 0), (0, 3)])
@@ -124,9 +121,10 @@ def test_render_forward_matches_oracle(dev, orc, mode, deg):
     rast, _, _ = _gpu_render(g, cams)
     ov = oracle_views(orc, g, cams)
     gimg = [x.cpu().numpy() for x in rast.split_images()]
-    bad, flagged, worst = compare_images(gimg, ov)
-    assert bad == 0, (bad, flagged, worst)
-    assert flagged < 0.08 * 128 * 96
+    bad, unchecked, worst = compare_images(gimg, ov)
+    print(f"forward: {bad} bad, {unchecked} unchecked of {128 * 96}, worst {worst:.2e}")
+    assert bad == 0, (bad, unchecked, worst)
+    assert unchecked < 0.02 * 128 * 96
     T = rast.split_pixels(rast.T_final)[0].cpu().numpy()
     nc = rast.split_pixels(rast.n_contrib)[0].cpu().numpy()
     fl = ov[0][4] < FLAG_MARGIN
@@ -180,9 +178,9 @@ def test_multiview_single_launch_matches_per_view_oracle(dev, orc):
     assert bad == 0, (bad, flagged, worst)
     rng = np.random.default_rng(3)
     ups = []
-    for (P, img, T, nc, mg) in ov:
-        u = rng.normal(size=img.shape) * 1e-3
-        u[mg < FLAG_MARGIN] = 0.0
+    for v in ov:
+        u = rng.normal(size=v.img.shape) * 1e-3
+        u[v.flag < FLAG_MARGIN] = 0.0
         ups.append(u)
     import torch
     dl = torch.from_numpy(np.concatenate([u.transpose(2, 0, 1).reshape(-1) for u in ups]).astype(np.float32)).to(dev)

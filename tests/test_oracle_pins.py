@@ -193,6 +193,34 @@ def test_front_to_back_order_and_occlusion(orc):
     assert T[0] == pytest.approx((1 - a1) * (1 - a2), abs=1e-14)
 
 
+def test_render_orders_enumerate_near_equal_depths(orc):
+    """Three Gaussians at depths within 1e-7 of each other cover the pixel: every one of the 3! orders
+    is a valid result, and each equals the closed-form front-to-back sum of that order; far apart
+    (1e-3) only the (depth, id) order is; the first listed colour is render()'s."""
+    import itertools
+    cols = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    cam = synth.camera(16, 16, time=0.5)
+    for gap, want_n in ((1e-7, 6), (1e-3, 1)):
+        gs = [_one([0, 0, 3.0 + k * gap, 0.5], np.log([0.3, 0.3, 0.3, 10]), [1, 0, 0, 0], [1, 0, 0, 0],
+                   opacity=0.5 - 0.4 * k, rgb=cols[k]) for k in range(3)]
+        g = {k: (np.concatenate([x[k] for x in gs]) if isinstance(gs[0][k], np.ndarray) else gs[0][k]) for k in gs[0]}
+        P = orc.project(g, cam)
+        alt, n_alt = orc.render_orders(P, cam, [8 * 16 + 8], 2e-6)
+        assert n_alt[0] == want_n
+        img, _, _, _ = orc.render(P, cam, pix=[8 * 16 + 8])
+        assert np.allclose(alt[0, 0], img[0], atol=1e-15)
+        a = [min(0.99, P[k, orc.P["ot"]] * math.exp(-0.5 * _q(P[k], 8.5, 8.5))) for k in range(3)]
+        want = set()
+        for perm in itertools.permutations(range(3)) if want_n == 6 else [(0, 1, 2)]:
+            C, T = np.zeros(3), 1.0
+            for k in perm:
+                C += T * a[k] * np.asarray(cols[k], float)
+                T *= 1 - a[k]
+            want.add(tuple(np.round(C, 12)))
+        got = {tuple(np.round(c, 12)) for c in alt[0, :n_alt[0]]}
+        assert got == want
+
+
 def _q(rec, x, y):
     C = {k: i for i, k in enumerate(
         ["visible", "u", "v", "depth", "ot", "ca", "cb", "cc"])}
@@ -439,37 +467,39 @@ def _blendable_tiles(P, i, C, W, H, tile=16):
     return set(t_of[blend].tolist()), set(t_of[q <= 9].tolist())
 
 
-def test_tile_pairs_cover_every_blendable_pixel_in_order(orc):
+def test_tile_lists_are_the_tiles_of_blendable_pixels_in_order(orc):
+    """Brute force over every pixel of the view: a Gaussian's tiles are exactly those holding a
+    pixel centre with q <= 9 and o_t exp(-q/2) >= 1/255 (up to the pairs the oracle marks as within
+    1e-4 of a threshold), listed by (tile, depth, id); fewer than the 3-sigma ellipse's tiles."""
     g = synth.gaussians_uniform(0)
-    cam = synth.camera(128, 96, time=0.5)
-    P = orc.project(g, cam)
-    tiles, ids = orc.tile_pairs(P, cam)
-    C = orc.P
-    # order: tile ascending, then depth, then id
-    key = list(zip(tiles, P[ids, C["depth"]], ids))
-    assert key == sorted(key)
-    have = {}
-    for t, i in zip(tiles.tolist(), ids.tolist()):
-        have.setdefault(i, set()).add(t)
-    need_total = sigma3_total = 0
-    for i in range(P.shape[0]):
-        need, sigma3 = _blendable_tiles(P, i, C, 128, 96)
-        assert need <= have.get(i, set()), i        # no blendable pixel is lost
-        if not need:
-            continue
-        need_total += len(need)
-        sigma3_total += len(sigma3)
-    # the rectangle is the box of an ellipse: a little larger than the tiles it needs, and smaller
-    # than the 3-sigma extent because low-opacity fragments fade below 1/255 before q = 9
-    assert need_total <= len(tiles) <= 1.5 * need_total
-    assert len(tiles) < sigma3_total
+    for cam, tile in ((synth.camera(128, 96, time=0.5), 16), (synth.camera(75, 41, 55.0, time=0.3), 8)):
+        W, H = cam["W"], cam["H"]
+        P = orc.project(g, cam)
+        tiles, ids, st = orc.tile_lists(P, cam, tile=(tile, tile), tile_offset=7)
+        C = orc.P
+        key = list(zip(tiles, P[ids, C["depth"]], ids))
+        assert key == sorted(key)
+        assert len(set(zip(tiles.tolist(), ids.tolist()))) == len(tiles)
+        have, maybe = {}, {}
+        for t, i, s_ in zip(tiles.tolist(), ids.tolist(), st.tolist()):
+            (have if s_ == 1 else maybe).setdefault(i, set()).add(t - 7)
+        need_total = sigma3_total = 0
+        for i in range(P.shape[0]):
+            need, sigma3 = _blendable_tiles(P, i, C, W, H, tile)
+            if P[i, C["visible"]] == 0:
+                need = set()
+            assert have.get(i, set()) <= need <= have.get(i, set()) | maybe.get(i, set()), i
+            need_total += len(need)
+            sigma3_total += len(sigma3) if need else 0
+        assert (st == 1).sum() <= need_total <= len(tiles) and (st == 2).sum() < 0.01 * len(tiles)
+        assert need_total < sigma3_total
 
 
-def test_tile_rectangle_shrinks_with_temporal_opacity(orc):
-    """One isotropic Gaussian facing the camera, 4x4 tiles: the rectangle spans the tiles of the
-    pixels where the Gaussian can be blended, to within one tile per side.  At o_t = 0.2 those end
-    at q = 2 ln(51) < 9, inside the 3-sigma ellipse; just above the cull (o_t = 1.02/255) they end
-    at 0.2 sigma; at o_t = 0.99 the 3-sigma ellipse binds."""
+def test_tile_lists_shrink_with_temporal_opacity_in_closed_form(orc):
+    """One isotropic Gaussian facing the camera (pixel-space standard deviation s_px), 4x4 tiles:
+    it can be blended out to radius s_px sqrt(min(9, 2 ln(255 o_t))), so its tiles span the tiles of
+    the pixel centres inside that disc: at o_t = 0.2 less than the 3-sigma disc, just above the
+    cull (o_t = 1.02/255) 0.2 sigma, at o_t = 0.99 the 3-sigma disc."""
     W = 1024
     cam = synth.camera(W, W, 60.0, time=0.5)
     C = orc.P
@@ -480,20 +510,20 @@ def test_tile_rectangle_shrinks_with_temporal_opacity(orc):
         g = dict(mean4=np.array([[0.0, 0.0, 3.0, 0.5]]), logscale4=np.log([[0.3, 0.3, 0.3, 1e3]]),
                  ql=np.array([[1.0, 0, 0, 0]]), qr=np.array([[1.0, 0, 0, 0]]), opacity=np.array([logit]),
                  rgb=np.ones((1, 3)), sh=np.zeros((1, 0, 3)), sh_deg=0, mode=0)
-        P = orc.project(g, cam, tile=(4, 4))
+        P = orc.project(g, cam)
         assert P[0, C["ot"]] == pytest.approx(ot, rel=1e-6)
-        dx, dy = xs + 0.5 - P[0, C["u"]], ys + 0.5 - P[0, C["v"]]
-        q = P[0, C["ca"]] * dx * dx + 2 * P[0, C["cb"]] * dx * dy + P[0, C["cc"]] * dy * dy
-        blend = (q <= 9) & (ot * np.exp(-0.5 * q) >= 1 / 255)
-        bx, by = xs[blend] // 4, ys[blend] // 4
-        x0, x1, y0, y1 = (int(P[0, C[k]]) for k in ("x0", "x1", "y0", "y1"))
-        assert x0 <= bx.min() and bx.max() < x1 and y0 <= by.min() and by.max() < y1
-        assert x0 >= bx.min() - 1 and x1 <= bx.max() + 2 and y0 >= by.min() - 1 and y1 <= by.max() + 2
-        s3 = xs[q <= 9] // 4
-        spans[ot] = (x1 - x0, s3.max() - s3.min() + 1)
-    assert spans[0.2][0] < spans[0.2][1] - 2           # narrower than the 3-sigma extent
-    assert spans[1.02 / 255][0] < spans[0.2][0] / 5      # sigma sqrt(2 ln 1.02) = 0.2 sigma
-    assert spans[0.99][0] >= spans[0.99][1]
+        s_px = cam["fx"] * 0.3 / 3.0                       # focal length x scale / depth
+        s_px = math.sqrt(s_px * s_px + 0.3)                # plus the 0.3 px^2 dilation
+        rho = s_px * math.sqrt(min(9.0, 2 * math.log(255 * ot)))
+        inside = (xs + 0.5 - P[0, C["u"]]) ** 2 + (ys + 0.5 - P[0, C["v"]]) ** 2 <= rho * rho * (1 - 1e-9)
+        want = set(((ys[inside] // 4) * (W // 4) + xs[inside] // 4).tolist())
+        tiles, ids, st = orc.tile_lists(P, cam, tile=(4, 4))
+        assert set(tiles[st == 1].tolist()) <= want <= set(tiles.tolist())
+        tx = np.unique(np.asarray(sorted(want)) % (W // 4))
+        spans[ot] = (len(tx), rho)
+    assert spans[0.2][0] < 2 * 3 * s_px / 4 - 2            # narrower than the 3-sigma disc
+    assert spans[1.02 / 255][0] < spans[0.2][0] / 5        # 0.2 sigma
+    assert abs(spans[0.99][0] - 2 * 3 * s_px / 4) <= 2     # the 3-sigma disc binds
 
 
 # ---------------------------------------------------------------------------------------------
@@ -511,6 +541,62 @@ def test_backprojection_round_trip(orc):
         # the float32 rotation is orthonormal only to ~1e-7, which bounds the round trip
         assert np.allclose(u, xs + 0.5, atol=1e-4) and np.allclose(v, ys + 0.5, atol=1e-4)
         assert np.allclose(xc[:, 2], vid["depth"][f].reshape(-1), rtol=1e-6)
+
+
+def _cam_f32(cam):
+    """The camera as the float32 values a device-side camera struct holds (kept as float64)."""
+    out = dict(cam)
+    out["R"] = np.asarray(cam["R"], np.float32).astype(np.float64)
+    out["t"] = np.asarray(cam["t"], np.float32).astype(np.float64)
+    for k in ("fx", "fy", "cx", "cy"):
+        out[k] = float(np.float32(cam[k]))
+    return out
+
+
+def test_backprojection_f32_within_rounding_bound_of_f64(orc):
+    """The float32 reading of Eq. 5 (a fixed sequence of correctly rounded float32 operations) lies
+    within the forward-error bound of that sequence from the float64 back-projection of the same
+    (float32-rounded) camera and depth: with u = 2^-24, X_c,x carries at most 3 roundings
+    (subtract, divide, multiply), d_j = X_c,j - tau_j one more, and each output two products' and
+    two sums' worth, so |X32_a - X64_a| <= 8 u sum_j |W_ja| (|X_c,j| + |tau_j|).  A dropped term, a
+    wrong sign or a transposed rotation moves a point by ~|W_ja d_j|, orders of magnitude more."""
+    vid = synth.depth_video(2, n_frames=200, W=96, H=54, frames=[0, 77, 199])
+    u = 2.0 ** -24
+    ys, xs = np.divmod(np.arange(96 * 54), 96)
+    for f in range(3):
+        cam = _cam_f32(vid["cams"][f])
+        X64 = orc.backproject(cam, vid["depth"][f])
+        X32 = orc.backproject_f32(cam, vid["depth"][f])
+        assert X32.dtype == np.float32
+        D = vid["depth"][f].reshape(-1).astype(np.float64)
+        Xc = np.c_[D * (xs + 0.5 - cam["cx"]) / cam["fx"], D * (ys + 0.5 - cam["cy"]) / cam["fy"], D]
+        R = np.asarray(cam["R"], np.float64)
+        mag = (np.abs(Xc) + np.abs(cam["t"])[None, :]) @ np.abs(R)   # sum_j |W_ja| (|X_c,j| + |tau_j|)
+        err = np.abs(X32.astype(np.float64) - X64)
+        assert np.all(err <= 8 * u * mag), float((err / (u * mag)).max())
+        # the bound is not vacuous: the float32 result is not the float64 one rounded at the end
+        assert (X32.astype(np.float64) != X64.astype(np.float32).astype(np.float64)).any()
+    # the video helper concatenates frames in point order f*H*W + py*W + px
+    cat = orc.backproject_video_f32(vid)
+    assert np.array_equal(cat[96 * 54:2 * 96 * 54], orc.backproject_f32(vid["cams"][1], vid["depth"][1]))
+
+
+def test_backprojection_f32_single_pixel_by_hand(orc):
+    """One pixel of the float32 sequence worked through with numpy float32 scalars in the stated
+    order (every operation rounds to float32, none fused)."""
+    R = np.array([[0.8, -0.6, 0.0], [0.36, 0.48, -0.8], [0.48, 0.64, 0.6]])
+    cam = dict(R=R, t=np.array([0.1, -0.2, 0.3]), fx=500.0, fy=510.0, cx=320.0, cy=180.0, W=4, H=3, time=0.0)
+    depth = np.full((3, 4), 2.5, np.float32)
+    depth[2, 3] = np.float32(3.1)
+    out = orc.backproject_f32(cam, depth)[2 * 4 + 3]
+    f = np.float32
+    D = f(3.1)
+    xc = D * ((f(3) + f(0.5) - f(320.0)) / f(500.0))
+    yc = D * ((f(2) + f(0.5) - f(180.0)) / f(510.0))
+    d = [xc - f(0.1), yc - f(-0.2), D - f(0.3)]
+    Rf = R.astype(np.float32)
+    want = [(Rf[0, a] * d[0] + Rf[1, a] * d[1]) + Rf[2, a] * d[2] for a in range(3)]
+    assert np.array_equal(out, np.array(want, np.float32))
 
 
 @pytest.mark.parametrize("min_support", [1, 2, 5])
