@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--eager", action="store_true", help="launch the step eagerly instead of a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=4)
-    ap.add_argument("--tile", default="auto", help="screen tile WxH, or auto (time the candidates)")
+    ap.add_argument("--tile", default="auto", help="screen tile WxH, or auto (time the candidate tiles and batches)")
+    ap.add_argument("--batch", type=int, default=32, help="forward staging batch when --tile is not auto")
     ap.add_argument("--loss", choices=["l1+dssim", "l1"], default="l1+dssim",
                     help="photometric loss: the standard 3DGS (1 - 0.2) L1 + 0.2 D-SSIM, or L1 alone")
     ap.add_argument("--configs", action="store_true",
@@ -540,11 +541,11 @@ def run_ours(args, ws, rank, local):
         fa, fb = batches[0]
         cams0 = torch.cat([wl["cam_bank"][FULL][torch.as_tensor(fa)], wl["cam_bank"][HALF][torch.as_tensor(fb)]])
         tgt0 = torch.cat([wl["bank"][FULL][torch.as_tensor(fa)].reshape(-1), wl["bank"][HALF][torch.as_tensor(fb)].reshape(-1)])
-        tile, tune = autotune.tune_tile(wl["params"], n, sizes, cams0, tgt0, dssim=dssim)
+        (tile, batch), tune = autotune.tune(wl["params"], n, sizes, cams0, tgt0, dssim=dssim)
     else:
-        tile = tuple(int(x) for x in args.tile.split("x"))
+        tile, batch = tuple(int(x) for x in args.tile.split("x")), args.batch
     step = T.TrainStep(wl["params"], n, 0, 0, sizes, steps=max(total_steps, 2000), loss_kind=L.LOSS_L1,
-                       capacity=16 * n, tile=tile, dssim=dssim)
+                       capacity=16 * n, tile=tile, dssim=dssim, batch=batch)
     fullpix, halfpix = 3 * FULL[0] * FULL[1], 3 * HALF[0] * HALF[1]
     tgt_full = step.target[:N_FULL * fullpix].view(N_FULL, fullpix)
     tgt_half = step.target[N_FULL * fullpix:].view(N_HALF, halfpix)
@@ -630,7 +631,13 @@ def run_ours(args, ws, rank, local):
     I = int(step.rast.n_inst.item())
     R_vis = int((step.rast.touched[:V * n] > 0).sum().item())
     P = step.rast.total_pixels
-    E = int(step.rast.n_contrib[:P].to(torch.int64).sum().item())  # blended pairs of the last step
+    # blended pairs of the last batch: the step itself does not count them, so one extra forward does
+    step.rast.count = True
+    step.rast.project(step.params, step.cams)
+    step.rast.bin()
+    step.rast.composite()
+    E = int(step.rast.n_contrib[:P].to(torch.int64).sum().item())
+    step.rast.count = False
     bits = 32 + int(np.ceil(np.log2(max(step.rast.total_tiles, 2))))
     passes = (bits + 7) // 8
     per_step = {k: v[0] / args.profile_steps for k, v in prof.items()}
@@ -672,7 +679,8 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic (seeded room depth video + hidden 4D Gaussian scene; no dataset)",
         "config": {"workload": "train_step_1M_8views", "n_gaussians": n, "n_dynamic": wl["n_dynamic"],
                    "views": "4x960x540+4x480x270", "tile": f"{tile[0]}x{tile[1]}",
-                   "tile_ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tune.items()} if tune else None,
+                   "batch": batch or 32,
+                   "tile_batch_ms": {f"{a}x{b}/{c}": round(v, 3) for ((a, b), c), v in tune.items()} if tune else None,
                    "init": "heuristic, 3-NN spatial scale",
                    "loss": "(1 - 0.2) L1 + 0.2 D-SSIM" if dssim > 0 else "L1",
                    "graph": not args.eager, "parallelism": f"replicas x{ws}",

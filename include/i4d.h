@@ -31,11 +31,13 @@
  *              Gaussian's SH group, i.e. plane 5 + (3k + c) / 4, lane (3k + c) % 4.
  *   A 4-vector (x, y, z, t) is the quaternion t + xi + yj + zk; R v = q_l v q_r (normalised q).
  *   Gradients use the same flat layout.
- *   Projected records: 4 planes of V x N float4 (view-major within a plane): plane 0 (u, v,
- *   conic_a, conic_b), plane 1 (conic_c, o_t, r, g), plane 2 (b, depth, radius, 0), plane 3 the
- *   blendable box: the pixel-space box (xmin, xmax, ymin, ymax) of the ellipse q <= q_b, with
- *   q_b = min(q_max, max(2 ln(o_t / alpha_min), 0) + 1e-3) the largest q at which alpha =
- *   o_t exp(-q/2) can reach alpha_min, widened by 1% + 0.01 px (empty (1, 0, 1, 0) when culled).
+ *   Projected records: V x N records of 64 bytes (view-major), each 4 float4: (xmin, xmax, ymin,
+ *   ymax) the blendable box: the pixel-space box of the ellipse q <= q_b, with q_b = min(q_max,
+ *   max(2 ln(o_t / alpha_min), 0) + 1e-3) the largest q at which alpha = o_t exp(-q/2) can reach
+ *   alpha_min, widened by 1% + 0.01 px (empty (1, 0, 1, 0) when culled); (u, v, k conic_a,
+ *   2 k conic_b); (k conic_c, o_t, m_thr, r); (g, b, depth, radius), with k = -log2(e) / 2 so that
+ *   exp(-q/2) = 2^(k q), and m_thr = k min(q_max, 2 ln(o_t / alpha_min)) (a fragment is kept where
+ *   k q >= m_thr).  The compositing kernels stage a record as it is: one 64-byte segment.
  *   2D gradients (scratch of the backward): 3 planes of V x N float4: (du, dv, dconic_a,
  *   dconic_b), (dconic_c, do_t, dr, dg), (db, 0, 0, 0).
  *   Images: per view, planar float32 [3][H][W]; views concatenated in order.  Per-pixel
@@ -66,7 +68,7 @@ extern "C" {
 #define I4D_ERR_WORKSPACE (-4) /* workspace smaller than *_workspace_size() */
 
 #define I4D_MAX_VIEWS 64
-#define I4D_PROJ_FLOATS 16     /* floats per projected record (4 float4 planes) */
+#define I4D_PROJ_FLOATS 16     /* floats per projected record (one 64-byte record) */
 #define I4D_GRAD2D_FLOATS 12   /* floats per (view, Gaussian) 2D-gradient record (3 float4 planes) */
 
 enum { I4D_MODE_FULL = 0, I4D_MODE_ISO_ROT = 1, I4D_MODE_ISO_IDENTITY = 2 };
@@ -119,9 +121,10 @@ typedef struct {
   float pad;
 } i4d_settings;
 
-/* Launch tuning (host); zeros select defaults. */
+/* Launch tuning of i4d_render_fwd (host); zeros select defaults.  The image does not depend on it. */
 typedef struct {
-  int32_t batch;        /* records staged in shared memory per round (render): 0 = tile pixels */
+  int32_t batch;        /* tile-list entries each warp tests and stages in shared memory per round:
+                           16, 32 or 64 (0 = 32); any other value is rejected with I4D_ERR_ARG */
   int32_t reserved[7];
 } i4d_tune;
 
@@ -157,7 +160,7 @@ I4D_API int64_t i4d_param_floats_sch(int32_t sh_deg, int32_t sch_terms);
  *   g        host struct, params on the device
  *   views    host; cams: DEVICE array of views->n_views cameras
  *   settings host (NULL = defaults)
- *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 4-plane record layout
+ *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 64-byte record layout
  *   touched  DEVICE out, n_views * n uint32: number of tiles of the record's rectangle
  *            (0 for culled or off-screen Gaussians)
  */
@@ -194,9 +197,12 @@ I4D_API int64_t i4d_total_pixels(const i4d_views* views);
  * ends before the fragment that would take T below T_min; C = sum T alpha rgb + T_final bg.
  *   img       DEVICE out, total_pixels * 3 floats (per view planar [3][H][W])
  *   T_final   DEVICE out, total_pixels floats
- *   last      DEVICE out, total_pixels uint32: 1 + position (within the tile's range) of the last
- *             blended fragment (0 if none) -- the backward resumes from here
- *   n_contrib DEVICE out, total_pixels uint32: fragments blended
+ *   last      DEVICE out, total_pixels uint32: the position (within the tile's range) where the
+ *             pixel's walk ended -- the fragment that would have taken T below T_min, or the list
+ *             length; the pixel blended exactly its kept fragments before it (the backward resumes
+ *             from here)
+ *   n_contrib DEVICE out, total_pixels uint32: fragments blended; NULL skips the count
+ *   tune      host, nullable: i4d_tune.batch (I4D_ERR_ARG for an unsupported value)
  */
 I4D_API int32_t i4d_render_fwd(const i4d_views* views, int32_t n, const float* proj, const uint32_t* ids,
                        const uint32_t* ranges, const i4d_settings* settings, const i4d_tune* tune, float* img,

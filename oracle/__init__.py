@@ -159,22 +159,25 @@ def render(proj: np.ndarray, cam: dict, bg=(0.0, 0.0, 0.0), settings=None, pix=N
     return (img, T, nc, mg, dmg) if depth_margin else (img, T, nc, mg)
 
 
-def render_orders(proj: np.ndarray, cam: dict, pix, depth_margin: float, max_alt: int = 64, bg=(0.0, 0.0, 0.0),
-                  settings=None):
-    """Every valid colour of each pixel in `pix` when fragments whose depths differ by less than
-    depth_margin (relative) may come in either order: (alt (npix, max_alt, 3), n_alt (npix,)), n_alt =
-    the number of orders (alt[:, 0] is the (depth, id) order), -1 when there are more than max_alt."""
+def render_alternatives(proj: np.ndarray, cam: dict, pix, margin: float, depth_margin: float, impact_min: float,
+                        max_alt: int = 1024, bg=(0.0, 0.0, 0.0), settings=None):
+    """Every valid colour of each pixel in `pix` when its decisions within `margin` of a threshold
+    (coverage, alpha, cull, near plane, the T stop) may go either way and fragments whose depths
+    differ by less than depth_margin (relative) may come in either order, counting only decisions
+    whose flip moves the colour by more than impact_min: (alt (npix, max_alt, 3), n_alt (npix,)),
+    n_alt = the number of branches (alt[:, 0] is the computed one), -1 when there are too many."""
     lib = _load()
     S = settings if settings is not None else settings_array()
     pix_arr = np.ascontiguousarray(pix, dtype=np.int32)
     npix = pix_arr.shape[0]
     alt = np.zeros((npix, max_alt, 3), dtype=np.float64)
     n_alt = np.zeros(npix, dtype=np.int32)
-    rc = lib.orc_render_orders(proj.shape[0], _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)),
-                               _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), ctypes.c_double(depth_margin),
-                               int(max_alt), _ptr(alt), _ptr(n_alt))
+    rc = lib.orc_render_alternatives(proj.shape[0], _ptr(np.ascontiguousarray(proj)), _ptr(camera_array(cam)),
+                                     _ptr(_f64(bg)), _ptr(S), npix, _ptr(pix_arr), ctypes.c_double(margin),
+                                     ctypes.c_double(depth_margin), ctypes.c_double(impact_min), int(max_alt),
+                                     _ptr(alt), _ptr(n_alt))
     if rc != 0:
-        raise RuntimeError(f"orc_render_orders failed ({rc})")
+        raise RuntimeError(f"orc_render_alternatives failed ({rc})")
     return alt, n_alt
 
 

@@ -544,13 +544,16 @@ int orc_render(int n, const double* P, const double* cam, const double* bg, cons
 }
 
 /*
- * Fragments whose depths differ by less than depth_margin (relative) have no order a float32
- * pipeline can be held to: either order is a valid result of the (depth, id) sort.  For each pixel,
- * group the blended candidates into maximal runs of consecutive fragments (in (depth, id) order)
- * whose successive gaps are below depth_margin, and composite every order obtained by permuting
- * within the runs.  alt: npix x max_alt x 3 colours (the first is the (depth, id) order itself);
- * n_alt[j]: the number written, or -1 when the runs admit more than max_alt orders (alt then holds
- * only the first).
+ * Every valid colour of a pixel whose compositing takes decisions that a float32 evaluation may
+ * take the other way: (1) fragments whose depths differ by less than depth_margin (relative) have
+ * no order a float32 sort can be held to, so every order of each maximal run of such consecutive
+ * fragments (in (depth, id) order) is valid; (2) a fragment whose coverage, alpha, cull or
+ * near-plane decision lies within `margin` (relative) of its threshold may be blended or not;
+ * (3) a blend whose T(1 - alpha) lies within `margin` of T_min may stop the pixel or not.  A
+ * decision is branched on only where its flip could move the colour by more than impact_min (the
+ * fragment's weight T alpha max(1, |c|), as in decision_margins; a run is permuted only when two of
+ * its fragments carry that much weight in the (depth, id) order).  The colours of all branches are
+ * written; the first is the (depth, id) order with every decision taken as computed.
  */
 static int factorial(int g) { int f = 1; for (int k = 2; k <= g; ++k) f *= k; return f; }
 
@@ -567,67 +570,156 @@ static void nth_permutation(int g, int idx, int* perm) {
   }
 }
 
-int orc_render_orders(int n, const double* P, const double* cam, const double* bg, const double* S, int npix,
-                      const int* pix, double depth_margin, int max_alt, double* alt, int* n_alt) {
+typedef struct {
+  const double *P, *S, *bg;
+  const frag* f;
+  int cnt;
+  const int* run_len;      /* > 1 at the first fragment of a permuted run, else 1 */
+  double margin, impact_min;
+  int max_alt, n_out;      /* n_out > max_alt: too many branches */
+  double* out;
+} alt_walk;
+
+static void alt_leaf(alt_walk* w, const double C[3], double T) {
+  if (w->n_out < w->max_alt)
+    for (int ch = 0; ch < 3; ++ch) w->out[3 * w->n_out + ch] = C[ch] + T * w->bg[ch];
+  w->n_out++;
+}
+
+/* outcomes of one fragment: (T after, colour after, stopped); returns their number (1..3) */
+static int frag_outcomes(const alt_walk* w, const frag* fr, double T, const double C[3], double To[3],
+                         double Co[3][3], int stop[3]) {
+  const double* r = w->P + (size_t)fr->id * P_STRIDE;
+  const double weight = T * fr->alpha * colour_scale(r);
+  const int matters = weight > w->impact_min;
+  int no = 0;
+  const int blend_opts = (fr->margin < w->margin && matters) ? 2 : 1;
+  for (int b = 0; b < blend_opts; ++b) {
+    const int blend = blend_opts == 2 ? b : fr->kept;
+    if (!blend) {
+      To[no] = T; stop[no] = 0;
+      for (int ch = 0; ch < 3; ++ch) Co[no][ch] = C[ch];
+      ++no;
+      continue;
+    }
+    const double Tn = T * (1.0 - fr->alpha);
+    const int canon_stop = Tn < w->S[S_T_MIN];
+    const int stop_opts = (rel_margin(Tn, w->S[S_T_MIN]) < w->margin && matters) ? 2 : 1;
+    for (int q = 0; q < stop_opts; ++q) {
+      const int st = stop_opts == 2 ? q : canon_stop;
+      stop[no] = st;
+      if (st) {
+        To[no] = T;
+        for (int ch = 0; ch < 3; ++ch) Co[no][ch] = C[ch];
+      } else {
+        To[no] = Tn;
+        Co[no][0] = C[0] + T * fr->alpha * r[P_R];
+        Co[no][1] = C[1] + T * fr->alpha * r[P_G];
+        Co[no][2] = C[2] + T * fr->alpha * r[P_B];
+      }
+      ++no;
+    }
+  }
+  return no;
+}
+
+static void alt_from(alt_walk* w, int k, double T, const double C[3]);
+
+/* process the fragments seq[j..g) in that order, then continue in (depth, id) order from k_after */
+static void alt_seq(alt_walk* w, const int* seq, int j, int g, int k_after, double T, const double C[3]) {
+  if (w->n_out > w->max_alt) return;
+  if (j == g) { alt_from(w, k_after, T, C); return; }
+  double To[3], Co[3][3];
+  int stop[3];
+  const int no = frag_outcomes(w, &w->f[seq[j]], T, C, To, Co, stop);
+  for (int o = 0; o < no; ++o) {
+    if (stop[o]) alt_leaf(w, Co[o], To[o]);
+    else alt_seq(w, seq, j + 1, g, k_after, To[o], Co[o]);
+  }
+}
+
+static void alt_from(alt_walk* w, int k, double T, const double C[3]) {
+  if (w->n_out > w->max_alt) return;
+  if (k == w->cnt) { alt_leaf(w, C, T); return; }
+  const int g = w->run_len[k];
+  if (g > 1) {
+    int perm[8], seq[8];
+    for (int p = 0; p < factorial(g); ++p) {
+      nth_permutation(g, p, perm);
+      for (int m = 0; m < g; ++m) seq[m] = k + perm[m];
+      alt_seq(w, seq, 0, g, k + g, T, C);
+      if (w->n_out > w->max_alt) return;
+    }
+    return;
+  }
+  double To[3], Co[3][3];
+  int stop[3];
+  const int no = frag_outcomes(w, &w->f[k], T, C, To, Co, stop);
+  for (int o = 0; o < no; ++o) {
+    if (stop[o]) alt_leaf(w, Co[o], To[o]);
+    else alt_from(w, k + 1, To[o], Co[o]);
+  }
+}
+
+/*
+ * alt: npix x max_alt x 3 colours; n_alt[j]: how many (>= 1), or -1 when the branches exceed
+ * max_alt (alt then holds the first max_alt).  Runs longer than 7 fragments are not permuted and
+ * make the pixel -1.
+ */
+int orc_render_alternatives(int n, const double* P, const double* cam, const double* bg, const double* S, int npix,
+                            const int* pix, double margin, double depth_margin, double impact_min, int max_alt,
+                            double* alt, int* n_alt) {
   const int W = (int)cam[C_W], H = (int)cam[C_H];
   if ((pix == NULL && npix != W * H) || max_alt < 1) return -1;
   int err = 0;
 #pragma omp parallel
   {
     frag* buf = (frag*)malloc(sizeof(frag) * (size_t)(n > 0 ? n : 1));
-    frag* tmp = (frag*)malloc(sizeof(frag) * (size_t)(n > 0 ? n : 1));
-    int* run_start = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int* run_len = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    if (!buf || !tmp || !run_start || !run_len) {
+    double* wgt = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!buf || !run_len || !wgt) {
 #pragma omp atomic write
       err = -2;
     }
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 4)
     for (int j = 0; j < npix; ++j) {
       if (err) continue;
       const int p = pix ? pix[j] : j;
-      int cnt = compact_kept(buf, gather_pixel(n, P, S, p % W, p / W, buf));
-      /* runs of near-equal depth (only those of two or more fragments are permuted) */
-      int nruns = 0;
-      long orders = 1;
+      const int cnt = gather_pixel(n, P, S, p % W, p / W, buf);
+      /* weights T alpha max(1, |c|) of the candidates in the (depth, id) walk (0 after its stop) */
+      double T = 1.0;
+      for (int k = 0; k < cnt; ++k) {
+        const double* r = P + (size_t)buf[k].id * P_STRIDE;
+        wgt[k] = T * buf[k].alpha * colour_scale(r);
+        if (buf[k].kept && T > 0.0) {
+          const double Tn = T * (1.0 - buf[k].alpha);
+          T = Tn < S[S_T_MIN] ? 0.0 : Tn;
+        }
+      }
+      int too_long = 0;
       for (int k = 0; k < cnt;) {
         int e = k + 1;
         while (e < cnt && fabs(buf[e].depth - buf[e - 1].depth) < depth_margin * fabs(buf[e - 1].depth)) ++e;
-        if (e - k > 1) {
-          run_start[nruns] = k;
-          run_len[nruns] = e - k;
-          orders = (e - k > 7 || orders > max_alt) ? (long)max_alt + 1 : orders * factorial(e - k);
-          ++nruns;
-        }
+        int heavy = 0;
+        for (int m = k; m < e; ++m) heavy += wgt[m] > impact_min;
+        run_len[k] = (e - k > 1 && heavy > 1) ? e - k : 1;
+        if (run_len[k] > 7) too_long = 1;
+        for (int m = k + 1; m < e; ++m) run_len[m] = 1;
+        if (run_len[k] == 1) e = k + 1;
         k = e;
       }
-      double C[3], T;
-      double* out = alt + (size_t)j * max_alt * 3;
-      composite(P, S, buf, cnt, bg, C, &T);
-      for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch];
-      if (orders > max_alt) {
+      alt_walk w = {P, S, bg, buf, cnt, run_len, margin, impact_min, max_alt, 0, alt + (size_t)j * max_alt * 3};
+      if (too_long) {
         n_alt[j] = -1;
         continue;
       }
-      for (long o = 1; o < orders; ++o) {
-        memcpy(tmp, buf, sizeof(frag) * (size_t)cnt);
-        long rem = o;
-        for (int r = 0; r < nruns; ++r) {
-          const int g = run_len[r], f = factorial(g);
-          int perm[8];
-          nth_permutation(g, (int)(rem % f), perm);
-          rem /= f;
-          for (int k = 0; k < g; ++k) tmp[run_start[r] + k] = buf[run_start[r] + perm[k]];
-        }
-        composite(P, S, tmp, cnt, bg, C, &T);
-        for (int ch = 0; ch < 3; ++ch) out[3 * o + ch] = C[ch];
-      }
-      n_alt[j] = (int)orders;
+      const double C0[3] = {0.0, 0.0, 0.0};
+      alt_from(&w, 0, 1.0, C0);
+      n_alt[j] = w.n_out > max_alt ? -1 : w.n_out;
     }
     free(buf);
-    free(tmp);
-    free(run_start);
     free(run_len);
+    free(wgt);
   }
   return err;
 }

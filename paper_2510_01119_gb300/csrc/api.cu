@@ -160,8 +160,10 @@ int32_t i4d_render_fwd(const i4d_views* views, int32_t n, const float* proj, con
                        float* T_final, uint32_t* last, uint32_t* n_contrib, void* stream) {
   ViewTable vt;
   if (!make_view_table(views, vt) || n < 0) return I4D_ERR_ARG;
-  if (!proj || !ids || !ranges || !img || !T_final || !last || !n_contrib) return I4D_ERR_ARG;
-  return cuda_status(launch_render_fwd(vt, n, proj, ids, ranges, to_settings(settings), tune ? tune->batch : 0, img,
+  if (!proj || !ids || !ranges || !img || !T_final || !last) return I4D_ERR_ARG;
+  const int batch = tune ? tune->batch : 0;
+  if (batch != 0 && batch != 16 && batch != 32 && batch != 64) return I4D_ERR_ARG;
+  return cuda_status(launch_render_fwd(vt, n, proj, ids, ranges, to_settings(settings), batch ? batch : 32, img,
                                        T_final, last, n_contrib, (cudaStream_t)stream));
 }
 

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) visible_compact_kernel(int64_t VN, const 
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= VN || touched[r] == 0) return;
   const uint32_t k = offs[r];
-  keys[k] = __float_as_uint(proj[2 * VN + r].y);  // positive depths: float bits order as the values
+  keys[k] = __float_as_uint(proj[4 * r + 3].z);  // positive depths: float bits order as the values
   vals[k] = (uint32_t)r;
 }
 
@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, c
                                                           const uint32_t* __restrict__ rec,
                                                           const uint32_t* __restrict__ offs, int64_t capacity,
                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t VN = (int64_t)vt.n_views * n;
   const int64_t R = *R_dev;
   const int lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,7 +172,8 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(ViewTable vt, int n, c
     const int v = (int)(r / (uint32_t)n);
     id = r - (uint32_t)v * (uint32_t)n;
     int x1, y1;
-    box_rect(proj[3 * VN + r], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+    box_rect(proj[4 * (size_t)r], vt.width[v], vt.height[v], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0,
+             y0, x1, y1);
     if (x1 > x0 && y1 > y0) {
       w = x1 - x0;
       cnt = w * (y1 - y0);

@@ -53,13 +53,21 @@ I4D_D int view_of_tile(const ViewTable& vt, int tile) {
 
 // Tile rectangle [x0, x1) x [y0, y1) of the square of half-width `radius` around (u, v).
 // The same function is used when counting and when emitting, so both agree bit for bit.
-I4D_D void box_rect(float4 b, int tile_w, int tile_h, int tiles_x, int tiles_y, int& x0, int& y0, int& x1,
-                    int& y1) {
-  // tiles [x0,x1) x [y0,y1) holding the pixels whose centres (p + 0.5) lie in the box
-  const float fx0 = floorf((b.x + 0.5f) / (float)tile_w);
-  const float fx1 = floorf((b.y - 0.5f) / (float)tile_w) + 1.0f;
-  const float fy0 = floorf((b.z + 0.5f) / (float)tile_h);
-  const float fy1 = floorf((b.w - 0.5f) / (float)tile_h) + 1.0f;
+I4D_D void box_rect(float4 b, int W, int H, int tile_w, int tile_h, int tiles_x, int tiles_y, int& x0, int& y0,
+                    int& x1, int& y1) {
+  // tiles [x0,x1) x [y0,y1) holding the pixels of the W x H view whose centres (p + 0.5) lie in the
+  // box: the box is first clipped to the view's pixel centres [0.5, W - 0.5] x [0.5, H - 0.5], so a
+  // box beyond the view's edge gets no tile even where the edge tiles reach past it
+  const float bx0 = fmaxf(b.x, 0.5f), bx1 = fminf(b.y, (float)W - 0.5f);
+  const float by0 = fmaxf(b.z, 0.5f), by1 = fminf(b.w, (float)H - 0.5f);
+  if (!(bx0 <= bx1 && by0 <= by1)) {
+    x0 = x1 = y0 = y1 = 0;
+    return;
+  }
+  const float fx0 = floorf((bx0 + 0.5f) / (float)tile_w);
+  const float fx1 = floorf((bx1 - 0.5f) / (float)tile_w) + 1.0f;
+  const float fy0 = floorf((by0 + 0.5f) / (float)tile_h);
+  const float fy1 = floorf((by1 - 0.5f) / (float)tile_h) + 1.0f;
   x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)tiles_x);
   x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)tiles_x);
   y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)tiles_y);

@@ -73,60 +73,66 @@ struct WarpPix {
   }
 };
 
-// The staged form of a record: mean, conic pre-scaled by kFalloff (see eval_pair), opacity, colour,
-// list position, record index and the exponent threshold of the kept test.
-__device__ __forceinline__ void stage_entry(const float4* __restrict__ proj, size_t VN, uint32_t r, uint32_t pos,
-                                            const Settings& S, float4& a, float4& b, uint4& x) {
-  const float4 pa = __ldg(&proj[r]);
-  const float4 pb = __ldg(&proj[VN + r]);
-  const float c2 = __ldg(&proj[2 * VN + r]).x;
-  const float q_thr = fminf(S.q_max, 2.0f * logf(pb.y / S.alpha_min));
-  a = make_float4(pa.x, pa.y, __fmul_rn(kFalloff, pa.z), __fmul_rn(2.0f * kFalloff, pa.w));
-  b = make_float4(__fmul_rn(kFalloff, pb.x), pb.y, pb.z, pb.w);
-  x = make_uint4(__float_as_uint(c2), pos, r, __float_as_uint(__fmul_rn(kFalloff, q_thr)));
+// The staged form of a record (slice_project writes it ready: 64 bytes, the box first): a = (u, v,
+// sa, sb2), b = (sc, o_t, m_thr, r), c = (g, b, list position bits, record index bits), with the
+// conic pre-scaled by kFalloff and m_thr the exponent threshold of the kept test (see eval_pair).
+// The box was read to test the entry; the other 48 bytes sit in the same 64-byte segment.
+__device__ __forceinline__ void stage_entry(const float4* __restrict__ proj, uint32_t r, uint32_t pos, float4& a,
+                                            float4& b, float4& c) {
+  a = __ldg(&proj[4 * (size_t)r + 1]);
+  b = __ldg(&proj[4 * (size_t)r + 2]);
+  const float4 t = __ldg(&proj[4 * (size_t)r + 3]);
+  c = make_float4(t.x, t.y, __uint_as_float(pos), __uint_as_float(r));
 }
 
-// A half-warp's staged hits of one chunk.
+// A half-warp's staged hits of one batch of B list entries.
+template <int B>
 struct HalfStage {
-  float4 a[32];
-  float4 b[32];
-  uint4 x[32];  // (colour b bits, list position, record, exponent threshold bits)
+  float4 a[B];
+  float4 b[B];
+  float4 c[B];
 };
 
-// Stage the chunk [lo, hi) of the tile list: every lane tests one entry against both halves' blocks
-// and writes a hit into the list of each half it meets, in list order.  Returns this half's count.
-template <class WP>
-__device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const float4* __restrict__ proj, size_t VN,
+// Stage the batch [lo, hi) of the tile list (hi - lo <= B): 32 entries at a time, every lane tests
+// one entry against both halves' blocks and writes a hit into the list of each half it meets, in
+// list order (B = 16 leaves the upper lanes idle).  Returns this half's count.
+template <int B, class WP>
+__device__ __forceinline__ int stage_batch(const WP& wp, HalfStage<B>* st, const float4* __restrict__ proj,
                                            const uint32_t* __restrict__ ids, uint32_t vbase, uint32_t lo, uint32_t hi,
-                                           uint32_t tile_start, int lane, int& other, const Settings& S) {
-  const uint32_t idx = lo + lane;
-  uint32_t r = 0;
-  bool hit0 = false, hit1 = false;
-  if (idx < hi) {
-    r = vbase + __ldg(&ids[idx]);
-    const float4 box = __ldg(&proj[3 * VN + r]);
-    hit0 = !wp.misses(box, 0);
-    hit1 = !wp.misses(box, 1);
-  }
-  const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
-  const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-  if (hit0 || hit1) {
-    const unsigned lt = (1u << lane) - 1u;
-    float4 a, b;
-    uint4 x;
-    stage_entry(proj, VN, r, idx - tile_start, S, a, b, x);
-    if (hit0) {
-      const int k = __popc(m0 & lt);
-      st[0].a[k] = a; st[0].b[k] = b; st[0].x[k] = x;
+                                           uint32_t tile_start, int lane, int& other) {
+  int c0 = 0, c1 = 0;
+#pragma unroll
+  for (int sub = 0; sub < (B + 31) / 32; ++sub) {
+    const uint32_t idx = lo + 32u * sub + lane;
+    uint32_t r = 0;
+    bool hit0 = false, hit1 = false;
+    if ((B >= 32 || lane < B) && idx < hi) {
+      r = vbase + __ldg(&ids[idx]);
+      const float4 box = __ldg(&proj[4 * (size_t)r]);
+      hit0 = !wp.misses(box, 0);
+      hit1 = !wp.misses(box, 1);
     }
-    if (hit1) {
-      const int k = __popc(m1 & lt);
-      st[1].a[k] = a; st[1].b[k] = b; st[1].x[k] = x;
+    const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+    const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+    if (hit0 || hit1) {
+      const unsigned lt = (1u << lane) - 1u;
+      float4 a, b, c;
+      stage_entry(proj, r, idx - tile_start, a, b, c);
+      if (hit0) {
+        const int k = c0 + __popc(m0 & lt);
+        st[0].a[k] = a; st[0].b[k] = b; st[0].c[k] = c;
+      }
+      if (hit1) {
+        const int k = c1 + __popc(m1 & lt);
+        st[1].a[k] = a; st[1].b[k] = b; st[1].c[k] = c;
+      }
     }
+    c0 += __popc(m0);
+    c1 += __popc(m1);
   }
   __syncwarp();
-  other = __popc(wp.half ? m0 : m1);
-  return __popc(wp.half ? m1 : m0);
+  other = wp.half ? c0 : c1;
+  return wp.half ? c1 : c0;
 }
 
 // The backward's staging: the chunk's entries that hit either half, stored once in list order, and
@@ -134,21 +140,20 @@ __device__ __forceinline__ int stage_chunk(const WP& wp, HalfStage* st, const fl
 struct SharedStage {
   float4 a[32];
   float4 b[32];
-  uint4 x[32];  // (colour b bits, list position, record, exponent threshold bits)
+  float4 c[32];
   uint8_t idx[2][32];
 };
 
 template <class WP>
 __device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st, const float4* __restrict__ proj,
-                                                  size_t VN, const uint32_t* __restrict__ ids, uint32_t vbase,
-                                                  uint32_t lo, uint32_t hi, uint32_t tile_start, int lane, int& other,
-                                                  const Settings& S) {
+                                                  const uint32_t* __restrict__ ids, uint32_t vbase, uint32_t lo,
+                                                  uint32_t hi, uint32_t tile_start, int lane, int& other) {
   const uint32_t idx = lo + lane;
   uint32_t r = 0;
   bool hit0 = false, hit1 = false;
   if (idx < hi) {
     r = vbase + __ldg(&ids[idx]);
-    const float4 box = __ldg(&proj[3 * VN + r]);
+    const float4 box = __ldg(&proj[4 * (size_t)r]);
     hit0 = !wp.misses(box, 0);
     hit1 = !wp.misses(box, 1);
   }
@@ -157,7 +162,7 @@ __device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st,
   if (hit0 || hit1) {
     const unsigned lt = (1u << lane) - 1u;
     const int k = __popc((m0 | m1) & lt);
-    stage_entry(proj, VN, r, idx - tile_start, S, st.a[k], st.b[k], st.x[k]);
+    stage_entry(proj, r, idx - tile_start, st.a[k], st.b[k], st.c[k]);
     if (hit0) st.idx[0][__popc(m0 & lt)] = (uint8_t)k;
     if (hit1) st.idx[1][__popc(m1 & lt)] = (uint8_t)k;
   }
@@ -173,88 +178,107 @@ constexpr int fwd_min_blocks() {
   return (TW * TH / 64) >= 36 ? 1 : (36 / (TW * TH / 64) > 32 ? 32 : 36 / (TW * TH / 64));
 }
 
-template <int TW, int TH>
+// COUNT: also write n_contrib, the number of fragments each pixel blended (an extra add per pixel and
+// fragment; the training step does not need it).  B: list entries each warp stages per round.
+template <int TW, int TH, bool COUNT, int B>
 __global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_fwd_kernel(ViewTable vt, int n, const float4* __restrict__ proj,
                                                                  const uint32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ ranges, Settings S,
                                                                  float* __restrict__ img, float* __restrict__ T_final,
-                                                                 uint32_t* __restrict__ last_out,
+                                                                 uint32_t* __restrict__ stop_out,
                                                                  uint32_t* __restrict__ ncon) {
-  __shared__ HalfStage stage[TW * TH / 64][2];
+  __shared__ HalfStage<B> stage[TW * TH / 64][2];
   const int T_all = vt.tile_off[vt.n_views];
   const int tile = (int)ranges[2 * T_all + blockIdx.x];
   const TileCoord tc = tile_coord(vt, tile);
   const WarpPix<TW> wp(tc, TH);
   const int lane = threadIdx.x & 31;
-  HalfStage* st = stage[threadIdx.x >> 5];
-  const HalfStage& mine = st[wp.half];
+  HalfStage<B>* st = stage[threadIdx.x >> 5];
+  const HalfStage<B>& mine = st[wp.half];
   const bool in0 = wp.px < tc.W && wp.py0 < tc.H;
   const bool in1 = wp.px < tc.W && wp.py0 + 1 < tc.H;
   const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
-  const size_t VN = (size_t)vt.n_views * n;
   const uint32_t vbase = (uint32_t)tc.v * (uint32_t)n;
   const float fx = (float)wp.px + 0.5f;
   const float2 fy = make_float2((float)wp.py0 + 0.5f, (float)wp.py0 + 1.5f);
-  // the thread's two pixels side by side in float2 lanes: transmittance and colour
-  float2 T = make_float2(1.0f, 1.0f);
+  // The thread's two pixels side by side in float2 lanes: transmittance and colour.  A pixel that
+  // stops keeps its final transmittance in Tf and goes on with T = 0 and a stop threshold of -1:
+  // every later fragment then has weight alpha * 0 = 0 (colour and T unchanged exactly) and cannot
+  // stop it again, so the hot loop needs no per-pixel "done" logic.  Pixels outside the view start
+  // stopped.
+  float2 T = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+  float2 thr = make_float2(in0 ? S.T_min : -1.0f, in1 ? S.T_min : -1.0f);
+  float2 Tf = T;
   float2 Cr = make_float2(0.0f, 0.0f), Cg = Cr, Cb = Cr;
-  uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
-  bool done0 = !in0, done1 = !in1;
-  for (uint32_t base = rs; base < re; base += 32) {
-    if (__all_sync(0xffffffffu, done0 && done1)) break;
+  uint32_t stop0 = in0 ? re - rs : 0u, stop1 = in1 ? re - rs : 0u;
+  uint32_t cnt0 = 0, cnt1 = 0;
+  for (uint32_t base = rs; base < re; base += B) {
+    if (__all_sync(0xffffffffu, thr.x < 0.0f && thr.y < 0.0f)) break;
     int other;
-    const int cnt = stage_chunk(wp, st, proj, VN, ids, vbase, base, min(base + 32u, re), rs, lane, other, S);
+    const int cnt = stage_batch<B>(wp, st, proj, ids, vbase, base, min(base + (uint32_t)B, re), rs, lane, other);
     for (int t = 0; t < cnt; ++t) {
       const float4 a = mine.a[t];
       const float4 b = mine.b[t];
-      const uint4 x = mine.x[t];
+      const float4 c = mine.c[t];
       const float dx = __fsub_rn(fx, a.x);
       FragPair f;
-      eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
-      const bool k0 = f.k0 && !done0, k1 = f.k1 && !done1;
-      // a kept fragment that would take T below T_min stops the pixel without being blended;
-      // T (1 - alpha) is formed as T - alpha T, so a pixel with weight 0 keeps T exactly
+      eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, b.z, S, f);
+      // weight alpha T of a kept fragment (T (1 - alpha) is formed as T - alpha T, so a weight of 0
+      // keeps T exactly)
       const float2 wk = __fmul2_rn(f.alpha, T);
-      const float2 Tn = __fadd2_rn(T, make_float2(-wk.x, -wk.y));
-      const bool s0 = k0 && Tn.x < S.T_min, s1 = k1 && Tn.y < S.T_min;
-      done0 = done0 || s0;
-      done1 = done1 || s1;
-      const bool b0 = k0 && !s0, b1 = k1 && !s1;
-      // a pixel that does not blend gets weight 0, which leaves its colour and T unchanged exactly
-      const float2 w = make_float2(b0 ? wk.x : 0.0f, b1 ? wk.y : 0.0f);
-      const float c2 = __uint_as_float(x.x);
-      Cr = __ffma2_rn(w, make_float2(b.z, b.z), Cr);
-      Cg = __ffma2_rn(w, make_float2(b.w, b.w), Cg);
-      Cb = __ffma2_rn(w, make_float2(c2, c2), Cb);
-      T = __fadd2_rn(T, make_float2(-w.x, -w.y));
-      const uint32_t p1 = x.y + 1u;
-      last0 = b0 ? p1 : last0;
-      last1 = b1 ? p1 : last1;
-      cnt0 += b0 ? 1u : 0u;
-      cnt1 += b1 ? 1u : 0u;
+      float2 w = make_float2(f.k0 ? wk.x : 0.0f, f.k1 ? wk.y : 0.0f);
+      float2 Tn = __fadd2_rn(T, make_float2(-w.x, -w.y));
+      if (Tn.x < thr.x || Tn.y < thr.y) {
+        // a kept fragment that would take T below T_min stops the pixel without being blended
+        if (Tn.x < thr.x) {
+          Tf.x = T.x;
+          stop0 = __float_as_uint(c.z);
+          thr.x = -1.0f;
+          w.x = 0.0f;
+          Tn.x = 0.0f;
+        }
+        if (Tn.y < thr.y) {
+          Tf.y = T.y;
+          stop1 = __float_as_uint(c.z);
+          thr.y = -1.0f;
+          w.y = 0.0f;
+          Tn.y = 0.0f;
+        }
+      }
+      Cr = __ffma2_rn(w, make_float2(b.w, b.w), Cr);
+      Cg = __ffma2_rn(w, make_float2(c.x, c.x), Cg);
+      Cb = __ffma2_rn(w, make_float2(c.y, c.y), Cb);
+      T = Tn;
+      if (COUNT) {
+        // a blended fragment has weight >= alpha_min T_min > 0
+        cnt0 += w.x != 0.0f ? 1u : 0u;
+        cnt1 += w.y != 0.0f ? 1u : 0u;
+      }
     }
     __syncwarp();
   }
+  if (thr.x >= 0.0f) Tf.x = T.x;
+  if (thr.y >= 0.0f) Tf.y = T.y;
   const int64_t HW = (int64_t)tc.W * tc.H;
   if (in0) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
-    img[pimg] = Cr.x + T.x * S.bg[0];
-    img[pimg + HW] = Cg.x + T.x * S.bg[1];
-    img[pimg + 2 * HW] = Cb.x + T.x * S.bg[2];
-    T_final[p] = T.x;
-    last_out[p] = last0;
-    ncon[p] = cnt0;
+    img[pimg] = Cr.x + Tf.x * S.bg[0];
+    img[pimg + HW] = Cg.x + Tf.x * S.bg[1];
+    img[pimg + 2 * HW] = Cb.x + Tf.x * S.bg[2];
+    T_final[p] = Tf.x;
+    stop_out[p] = stop0;
+    if (COUNT) ncon[p] = cnt0;
   }
   if (in1) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
     const int64_t pimg = 3 * vt.pix_off[tc.v] + (int64_t)(wp.py0 + 1) * tc.W + wp.px;
-    img[pimg] = Cr.y + T.y * S.bg[0];
-    img[pimg + HW] = Cg.y + T.y * S.bg[1];
-    img[pimg + 2 * HW] = Cb.y + T.y * S.bg[2];
-    T_final[p] = T.y;
-    last_out[p] = last1;
-    ncon[p] = cnt1;
+    img[pimg] = Cr.y + Tf.y * S.bg[0];
+    img[pimg + HW] = Cg.y + Tf.y * S.bg[1];
+    img[pimg + 2 * HW] = Cb.y + Tf.y * S.bg[2];
+    T_final[p] = Tf.y;
+    stop_out[p] = stop1;
+    if (COUNT) ncon[p] = cnt1;
   }
 }
 
@@ -377,7 +401,7 @@ __device__ __forceinline__ void phase_b(const BwdWarp& W, int half, int l16, int
     const int e = my_idx[glo + k];
     a = W.st.a[e];
     b = W.st.b[e];
-    rr = W.st.x[e].z;
+    rr = __float_as_uint(W.st.c[e].w);
     const float4(*sw)[kGroup] = W.sw[half];
     if (S == 1) {
       const float cx = __fsub_rn(bx0, a.x);
@@ -481,7 +505,7 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
   for (uint32_t hi = end; hi > rs;) {
     const uint32_t lo = (hi - rs > 32u) ? hi - 32u : rs;
     int other;
-    const int cnt = stage_chunk_shared(wp, W.st, proj, VN, ids, vbase, lo, hi, rs, lane, other, S);
+    const int cnt = stage_chunk_shared(wp, W.st, proj, ids, vbase, lo, hi, rs, lane, other);
     for (int ghi = max(cnt, other); ghi > 0; ghi -= kGroup) {  // warp-uniform
       const int glo = max(ghi - kGroup, 0);
       // ---- phase A: the recurrence, hits back to front ----
@@ -489,13 +513,15 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
         const int e = my_idx[t];
         const float4 a = stg.a[e];
         const float4 b = stg.b[e];
-        const uint4 x = stg.x[e];
+        const float4 c = stg.c[e];
         const float dx = __fsub_rn(fx, a.x);
         const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
         FragPair f;
-        eval_pair(dx, dy, a.z, a.w, b.x, b.y, __uint_as_float(x.w), S, f);
-        // the fragments a pixel blended are the kept ones before its last (out-of-view pixels: L = 0)
-        const bool k0 = f.k0 && x.y < P.L0, k1 = f.k1 && x.y < P.L1;
+        eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, S, f);
+        // the fragments a pixel blended are the kept ones before its stop position (out-of-view
+        // pixels: 0)
+        const uint32_t pos = __float_as_uint(c.z);
+        const bool k0 = f.k0 && pos < P.L0, k1 = f.k1 && pos < P.L1;
         const float2 na = __fmul2_rn(f.alpha, f2(-1.0f));
         const float2 om = __fadd2_rn(na, f2(1.0f));
         const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
@@ -503,7 +529,7 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
         const float2 nw = __fmul2_rn(make_float2(k0 ? na.x : 0.0f, k1 ? na.y : 0.0f), Tk);  // -alpha T_k
         // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
         // S_c the colour composited behind, T the transmittance behind
-        const float2 cr = f2(b.z), cg = f2(b.w), cb = f2(__uint_as_float(x.x));
+        const float2 cr = f2(b.w), cg = f2(c.x), cb = f2(c.y);
         const float2 yr = __ffma2_rn(P.T, cr, P.NSr);
         const float2 yg = __ffma2_rn(P.T, cg, P.NSg);
         const float2 yb = __ffma2_rn(P.T, cb, P.NSb);
@@ -534,15 +560,29 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
   }
 }
 
-template <int TW, int TH>
-cudaError_t launch_fwd_t(const ViewTable& vt, int n, const float* proj, const uint32_t* ids, const uint32_t* ranges,
-                         const Settings& S, float* img, float* T_final, uint32_t* last, uint32_t* n_contrib,
-                         cudaStream_t st) {
+template <int TW, int TH, int B>
+cudaError_t launch_fwd_tb(const ViewTable& vt, int n, const float* proj, const uint32_t* ids, const uint32_t* ranges,
+                          const Settings& S, float* img, float* T_final, uint32_t* last, uint32_t* n_contrib,
+                          cudaStream_t st) {
   const int tiles = vt.tile_off[vt.n_views];
   I4D_PROF("render_fwd", st);
-  render_fwd_kernel<TW, TH><<<tiles, TW * TH / 2, 0, st>>>(vt, n, reinterpret_cast<const float4*>(proj), ids,
-                                                            ranges, S, img, T_final, last, n_contrib);
+  const float4* pr = reinterpret_cast<const float4*>(proj);
+  if (n_contrib)
+    render_fwd_kernel<TW, TH, true, B><<<tiles, TW * TH / 2, 0, st>>>(vt, n, pr, ids, ranges, S, img, T_final, last,
+                                                                       n_contrib);
+  else
+    render_fwd_kernel<TW, TH, false, B><<<tiles, TW * TH / 2, 0, st>>>(vt, n, pr, ids, ranges, S, img, T_final,
+                                                                        last, nullptr);
   return cudaGetLastError();
+}
+
+template <int TW, int TH>
+cudaError_t launch_fwd_t(const ViewTable& vt, int n, const float* proj, const uint32_t* ids, const uint32_t* ranges,
+                         const Settings& S, int batch, float* img, float* T_final, uint32_t* last,
+                         uint32_t* n_contrib, cudaStream_t st) {
+  if (batch == 16) return launch_fwd_tb<TW, TH, 16>(vt, n, proj, ids, ranges, S, img, T_final, last, n_contrib, st);
+  if (batch == 64) return launch_fwd_tb<TW, TH, 64>(vt, n, proj, ids, ranges, S, img, T_final, last, n_contrib, st);
+  return launch_fwd_tb<TW, TH, 32>(vt, n, proj, ids, ranges, S, img, T_final, last, n_contrib, st);
 }
 
 template <int TW, int TH>
@@ -575,9 +615,8 @@ cudaError_t launch_bwd_t(const ViewTable& vt, int n, const float* proj, const ui
 cudaError_t launch_render_fwd(const ViewTable& vt, int n, const float* proj, const uint32_t* ids,
                               const uint32_t* ranges, const Settings& S, int batch, float* img, float* T_final,
                               uint32_t* last, uint32_t* n_contrib, cudaStream_t st) {
-  (void)batch;
   if (vt.tile_off[vt.n_views] == 0) return cudaSuccess;
-  I4D_TILE_DISPATCH(launch_fwd_t, vt, n, proj, ids, ranges, S, img, T_final, last, n_contrib, st);
+  I4D_TILE_DISPATCH(launch_fwd_t, vt, n, proj, ids, ranges, S, batch, img, T_final, last, n_contrib, st);
 }
 
 cudaError_t launch_render_bwd(const ViewTable& vt, int n, const float* proj, const uint32_t* ids,

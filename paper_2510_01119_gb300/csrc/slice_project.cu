@@ -47,7 +47,6 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
   GaussState G;
   gauss_setup(__ldg(&P[i]), __ldg(&P[(size_t)n + i]), __ldg(&P[2 * (size_t)n + i]), __ldg(&P[3 * (size_t)n + i]),
               __ldg(&P[4 * (size_t)n + i]), mode, G);
-  const size_t VN = (size_t)vt.n_views * n;
   for (int v = 0; v < vt.n_views; ++v) {
     ViewFwd F;
     view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F, nt);
@@ -57,14 +56,19 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
       // screen extent where a fragment can be blended (q <= q_max and alpha >= alpha_min)
       box = ellipse_box(F.u, F.v, F.conic[0], F.conic[1], F.conic[2], blend_q(F.ot, S));
       int x0, y0, x1, y1;
-      box_rect(box, vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
+      box_rect(box, vt.width[v], vt.height[v], vt.tile_w, vt.tile_h, vt.tiles_x[v], vt.tiles_y[v], x0, y0, x1, y1);
       cnt = (uint32_t)((x1 - x0) * (y1 - y0));
     }
     const size_t r = (size_t)v * n + i;
-    proj[r] = make_float4(F.u, F.v, F.conic[0], F.conic[1]);
-    proj[VN + r] = make_float4(F.conic[2], F.ot, fmaxf(F.raw[0], 0.0f), fmaxf(F.raw[1], 0.0f));
-    proj[2 * VN + r] = make_float4(fmaxf(F.raw[2], 0.0f), F.m[2], F.radius, 0.0f);
-    proj[3 * VN + r] = box;
+    // the record as the compositing kernels stage it: conic scaled by kFalloff (exp(-q/2) =
+    // 2^(sa dx^2 + sb2 dx dy + sc dy^2)) and the exponent threshold of the kept test
+    // m >= kFalloff min(q_max, 2 ln(o_t / alpha_min)), computed once here instead of at every staging
+    const float m_thr = F.visible ? __fmul_rn(kFalloff, fminf(S.q_max, 2.0f * logf(F.ot / S.alpha_min))) : 0.0f;
+    float4* rec = proj + 4 * r;
+    rec[0] = box;
+    rec[1] = make_float4(F.u, F.v, __fmul_rn(kFalloff, F.conic[0]), __fmul_rn(2.0f * kFalloff, F.conic[1]));
+    rec[2] = make_float4(__fmul_rn(kFalloff, F.conic[2]), F.ot, m_thr, fmaxf(F.raw[0], 0.0f));
+    rec[3] = make_float4(fmaxf(F.raw[1], 0.0f), fmaxf(F.raw[2], 0.0f), F.m[2], F.radius);
     touched[r] = cnt;
   }
 }

@@ -92,7 +92,9 @@ class Rasterizer:
     """Owns every device buffer of the forward/backward of one batch of views."""
 
     def __init__(self, n: int, sh_deg: int, mode: int, sizes, tile=(16, 16), capacity: int = None,
-                 settings: dict = None, device="cuda", sch_terms: int = 0):
+                 settings: dict = None, device="cuda", sch_terms: int = 0, batch: int = 0, count: bool = True):
+        """batch: list entries the forward stages per warp and round (16, 32, 64; 0 = 32); count:
+        write n_contrib (fragments blended per pixel) in the forward."""
         L.load()
         self.n, self.sh_deg, self.mode = int(n), int(sh_deg), int(mode)
         self.sch_terms = int(sch_terms)
@@ -102,6 +104,8 @@ class Rasterizer:
         self.views = L.make_views(self.sizes, self.tile)
         self.settings = L.default_settings(**(settings or {}))
         self.tune = L.Tune()
+        self.tune.batch = int(batch)
+        self.count = bool(count)
         self.V = len(self.sizes)
         self.total_tiles = int(L.load().i4d_total_tiles(ctypes.byref(self.views)))
         self.total_pixels = int(L.load().i4d_total_pixels(ctypes.byref(self.views)))
@@ -143,7 +147,7 @@ class Rasterizer:
 
     def composite(self):
         L.i4d_render_fwd(self.views, self.n, self.proj, self.ids, self.ranges, self.settings, self.tune, self.img,
-                         self.T_final, self.last, self.n_contrib)
+                         self.T_final, self.last, self.n_contrib if self.count else None)
 
     def forward(self, params: torch.Tensor, cams: torch.Tensor, check_capacity: bool = True) -> torch.Tensor:
         """slice_project -> bin_tiles -> render_fwd.  With check_capacity the instance count is read

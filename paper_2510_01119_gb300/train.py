@@ -52,10 +52,12 @@ class TrainStep:
 
     def __init__(self, params: torch.Tensor, n: int, sh_deg: int, mode: int, sizes, steps: int,
                  loss_kind: int = L.LOSS_L1, capacity: int = None, tile=(16, 16), lr: dict = None,
-                 dssim: float = 0.0, sch_terms: int = 0):
+                 dssim: float = 0.0, sch_terms: int = 0, batch: int = 0):
         self.params = params
         self.n, self.sh_deg, self.mode = n, sh_deg, mode
-        self.rast = Rasterizer(n, sh_deg, mode, sizes, tile=tile, capacity=capacity, sch_terms=sch_terms)
+        # the step needs no per-pixel fragment counts (Rasterizer.count can be switched on to read them)
+        self.rast = Rasterizer(n, sh_deg, mode, sizes, tile=tile, capacity=capacity, sch_terms=sch_terms,
+                               batch=batch, count=False)
         dev = params.device
         self.m = torch.zeros_like(params)
         self.v = torch.zeros_like(params)

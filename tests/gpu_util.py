@@ -24,16 +24,18 @@ def rel_l2(a, b):
 
 
 class OView(NamedTuple):
-    """The oracle's render of one view.  flag < FLAG_MARGIN: the pixel may legitimately differ
-    (a threshold decision or a depth order within margin); thr: the threshold part alone; alt /
-    n_alt: for pixels flagged only by near-equal depths, every valid colour (render_orders)."""
+    """The oracle's render of one view.  flag < FLAG_MARGIN: a decision of the pixel (a threshold,
+    the T stop or the order of near-equal depths) may go either way in float32; alt: for those
+    pixels, every valid colour (render_alternatives), or None when there are too many branches."""
     P: np.ndarray
     img: np.ndarray
     T: np.ndarray
     nc: np.ndarray
     flag: np.ndarray
-    thr: np.ndarray
     alt: dict
+
+
+MAX_ALT = 1024
 
 
 def oracle_views(orc, g, cams, settings=None, bg=(0, 0, 0)):
@@ -45,34 +47,57 @@ def oracle_views(orc, g, cams, settings=None, bg=(0, 0, 0)):
         W, H = int(cam["W"]), int(cam["H"])
         # one flag value per pixel: below FLAG_MARGIN means "may differ"
         flag = np.minimum(mg, dmg * (FLAG_MARGIN / DEPTH_MARGIN))
-        depth_only = np.nonzero((dmg < DEPTH_MARGIN) & (mg >= FLAG_MARGIN))[0]
+        flagged = np.nonzero(flag < FLAG_MARGIN)[0]
         alt = {}
-        if len(depth_only):
-            a, na = orc.render_orders(P, cam, depth_only, DEPTH_MARGIN, bg=bg, settings=settings)
-            alt = {int(p): a[k, :na[k]] for k, p in enumerate(depth_only) if na[k] > 0}
-        out.append(OView(P, img.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), flag.reshape(H, W),
-                         mg.reshape(H, W), alt))
+        if len(flagged):
+            a, na = orc.render_alternatives(P, cam, flagged, FLAG_MARGIN, DEPTH_MARGIN, IMPACT_MIN, MAX_ALT, bg=bg,
+                                            settings=settings)
+            alt = {int(p): (a[k, :na[k]] if na[k] > 0 else None) for k, p in enumerate(flagged)}
+        out.append(OView(P, img.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), flag.reshape(H, W), alt))
     return out
 
 
+def match_alternatives(got, alt):
+    """Max-abs error of each pixel of `got` (m, 3) against the closest of its valid colours (alt:
+    list of (k, 3) arrays or None); NaN where the alternatives were too many to list."""
+    err = np.full(len(got), np.nan)
+    for j, cols in enumerate(alt):
+        if cols is not None:
+            err[j] = np.abs(cols - got[j]).max(axis=1).min()
+    return err
+
+
 def compare_images(gpu_imgs, orc_views, what=""):
-    """gpu_imgs: list of (3,H,W) numpy.  Every pixel must match the oracle to IMG_TOL, except those
-    with a threshold decision within FLAG_MARGIN; a pixel whose fragments only have near-equal depths
-    must match one of the colours of their valid orders.  Returns (n_bad, n_unchecked, max_err)."""
+    """gpu_imgs: list of (3,H,W) numpy.  Every pixel must match the oracle to IMG_TOL; a pixel with
+    a decision that float32 may take either way must match one of its valid colours.  Returns
+    (n_bad, n_unchecked (too many branches to list), max_err)."""
     bad = unchecked = 0
     worst = 0.0
     for gi, ov in zip(gpu_imgs, orc_views):
-        H, W = ov.flag.shape
         got = gi.transpose(1, 2, 0).reshape(-1, 3)
         err = np.abs(got - ov.img.reshape(-1, 3)).max(axis=1)
-        flagged = ov.flag.reshape(-1) < FLAG_MARGIN
-        for p, cols in ov.alt.items():
-            err[p] = np.abs(cols - got[p]).max(axis=1).min()
-            flagged[p] = False
-        unchecked += int(flagged.sum())
-        worst = max(worst, float(err[~flagged].max()) if (~flagged).any() else 0.0)
-        bad += int(((err > IMG_TOL) & ~flagged).sum())
+        if ov.alt:
+            ps = np.fromiter(ov.alt.keys(), np.int64)
+            err[ps] = match_alternatives(got[ps], list(ov.alt.values()))
+        skip = np.isnan(err)
+        unchecked += int(skip.sum())
+        worst = max(worst, float(err[~skip].max()) if (~skip).any() else 0.0)
+        bad += int(((err > IMG_TOL) & ~skip).sum())
     return bad, unchecked, worst
+
+
+# exp(-q/2) = 2^(KFALLOFF q): the records carry the conic scaled by it (the record layout of i4d.h)
+KFALLOFF = -0.5 / np.log(2.0)
+
+
+def gpu_records(rast):
+    """The projected records of a Rasterizer as float64 columns (the 64-byte record layout of
+    i4d.h: box | u, v, sa, sb2 | sc, o_t, m_thr, r | g, b, depth, radius), conic unscaled."""
+    rec = rast.proj.view(-1, 4, 4).cpu().numpy().astype(np.float64)
+    k = KFALLOFF
+    return dict(box=rec[:, 0], u=rec[:, 1, 0], v=rec[:, 1, 1], ca=rec[:, 1, 2] / k, cb=rec[:, 1, 3] / (2 * k),
+                cc=rec[:, 2, 0] / k, ot=rec[:, 2, 1], m_thr=rec[:, 2, 2], r=rec[:, 2, 3], g=rec[:, 3, 0],
+                b=rec[:, 3, 1], depth=rec[:, 3, 2], radius=rec[:, 3, 3])
 
 
 def tile_lists_oracle(orc, views_P, cams, tile=(16, 16)):

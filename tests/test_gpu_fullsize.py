@@ -22,13 +22,14 @@ def dev():
 
 
 def _sampled_parity(orc, g, cams, n_pix, seed, dev, grad_keys, min_checked=0.95, tile_check=False):
-    """Forward: every sampled pixel matches the oracle to IMG_TOL, a pixel whose fragments have
-    near-equal depths matching one of the colours of their valid orders; only pixels with a
-    threshold decision within FLAG_MARGIN (or too many valid orders) go unchecked, and they must be
-    fewer than 1 - min_checked.  Backward: the gradient of a loss on the sampled pixels whose order
-    is unique, against the oracle's.  With tile_check, the whole (tile, id) list of the batch is
-    also checked against the oracle's binning."""
+    """Forward: every sampled pixel matches the oracle to IMG_TOL; a pixel with a decision that
+    float32 may take either way (a threshold, the T stop, the order of near-equal depths) must match
+    one of its valid colours, and only pixels with too many such branches to list go unchecked
+    (fewer than 1 - min_checked).  Backward: the gradient of a loss on the sampled pixels without
+    such decisions, against the oracle's.  With tile_check, the whole (tile, id) list of the batch
+    is also checked against the oracle's binning."""
     import torch
+    from gpu_util import MAX_ALT, match_alternatives
     from paper_2510_01119_gb300 import rasterizer as R
     n = g["mean4"].shape[0]
     rast = R.Rasterizer(n, g["sh_deg"], g.get("mode", 0), [(c["W"], c["H"]) for c in cams])
@@ -39,7 +40,7 @@ def _sampled_parity(orc, g, cams, n_pix, seed, dev, grad_keys, min_checked=0.95,
     rng = np.random.default_rng(seed)
     upstream, Ps = [], []
     want = None
-    bad = unchecked = by_order = 0
+    bad = unchecked = by_alt = 0
     worst = 0.0
     for v, cam in enumerate(cams):
         W, H = cam["W"], cam["H"]
@@ -47,34 +48,29 @@ def _sampled_parity(orc, g, cams, n_pix, seed, dev, grad_keys, min_checked=0.95,
         P = orc.project(g, cam)
         Ps.append(P)
         oimg, T, nc, mg, dmg = orc.render(P, cam, pix=pix, depth_margin=True, impact_min=IMPACT_MIN)
-        thr = mg < FLAG_MARGIN
-        dep = (dmg < DEPTH_MARGIN) & ~thr
+        fl = (mg < FLAG_MARGIN) | (dmg < DEPTH_MARGIN)
         got = imgs[v].reshape(3, -1)[:, pix].T
         err = np.abs(got - oimg).max(axis=1)
-        skip = thr.copy()
-        if dep.any():
-            alt, n_alt = orc.render_orders(P, cam, pix[dep], DEPTH_MARGIN)
-            for k, j in enumerate(np.nonzero(dep)[0]):
-                if n_alt[k] < 0:
-                    skip[j] = True
-                else:
-                    err[j] = np.abs(alt[k, :n_alt[k]] - got[j]).max(axis=1).min()
-            by_order += int((n_alt >= 0).sum())
+        if fl.any():
+            alt, n_alt = orc.render_alternatives(P, cam, pix[fl], FLAG_MARGIN, DEPTH_MARGIN, IMPACT_MIN, MAX_ALT)
+            err[fl] = match_alternatives(got[fl], [alt[k, :m] if m > 0 else None for k, m in enumerate(n_alt)])
+            by_alt += int((n_alt > 0).sum())
+        skip = np.isnan(err)
         bad += int(((err > IMG_TOL) & ~skip).sum())
         unchecked += int(skip.sum())
         worst = max(worst, float(err[~skip].max()))
         up = rng.normal(size=(n_pix, 3)) * 1e-2
-        up[thr | dep] = 0.0
+        up[fl] = 0.0
         dense = np.zeros((3, W * H), np.float32)
         dense[:, pix] = up.T
         upstream.append(dense.reshape(-1))
         _, gr = orc.render_bwd(g, cam, up, pix=pix)
         want = gr if want is None else {k: want[k] + gr[k] for k in want}
     total = n_pix * len(cams)
-    print(f"sampled pixels: {total}, unchecked {unchecked}, checked through valid orders {by_order}, "
+    print(f"sampled pixels: {total}, checked against their valid colours {by_alt}, unchecked {unchecked}, "
           f"worst {worst:.2e}")
-    assert bad == 0, (bad, unchecked, by_order)
-    assert total - unchecked >= min_checked * total, (unchecked, by_order)
+    assert bad == 0, (bad, unchecked, by_alt)
+    assert total - unchecked >= min_checked * total, (unchecked, by_alt)
     if tile_check:
         from gpu_util import check_tile_lists
         tiles, ids = rast.tile_lists()

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import FLAG_MARGIN, GRAD_TOL, compare_images, oracle_views, rel_l2
+from gpu_util import FLAG_MARGIN, GRAD_TOL, compare_images, gpu_records, oracle_views, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -42,12 +42,12 @@ def test_sch_forward_and_backward_match_oracle(dev, orc, deg, nt):
     assert bad == 0, (bad, flagged, worst)
     # records: the colour columns carry the SCH terms
     n = g["mean4"].shape[0]
-    planes = rast.proj.view(4, len(cams) * n, 4).cpu().numpy()
+    rec = gpu_records(rast)
     C = orc.P
     for v, cam in enumerate(cams):
         P = ov[v][0]
         vis = P[:, C["visible"]] != 0
-        got = np.c_[planes[1, v * n:(v + 1) * n, 2:4], planes[2, v * n:(v + 1) * n, 0]]
+        got = np.c_[rec["r"], rec["g"], rec["b"]][v * n:(v + 1) * n]
         want = P[:, [C["r"], C["g"], C["b"]]]
         assert np.abs(got[vis] - want[vis]).max() < 2e-6
     # backward, summed over both views

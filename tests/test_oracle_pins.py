@@ -193,7 +193,7 @@ def test_front_to_back_order_and_occlusion(orc):
     assert T[0] == pytest.approx((1 - a1) * (1 - a2), abs=1e-14)
 
 
-def test_render_orders_enumerate_near_equal_depths(orc):
+def test_render_alternatives_enumerate_near_equal_depths(orc):
     """Three Gaussians at depths within 1e-7 of each other cover the pixel: every one of the 3! orders
     is a valid result, and each equals the closed-form front-to-back sum of that order; far apart
     (1e-3) only the (depth, id) order is; the first listed colour is render()'s."""
@@ -205,7 +205,7 @@ def test_render_orders_enumerate_near_equal_depths(orc):
                    opacity=0.5 - 0.4 * k, rgb=cols[k]) for k in range(3)]
         g = {k: (np.concatenate([x[k] for x in gs]) if isinstance(gs[0][k], np.ndarray) else gs[0][k]) for k in gs[0]}
         P = orc.project(g, cam)
-        alt, n_alt = orc.render_orders(P, cam, [8 * 16 + 8], 2e-6)
+        alt, n_alt = orc.render_alternatives(P, cam, [8 * 16 + 8], 1e-4, 2e-6, 5e-5)
         assert n_alt[0] == want_n
         img, _, _, _ = orc.render(P, cam, pix=[8 * 16 + 8])
         assert np.allclose(alt[0, 0], img[0], atol=1e-15)
@@ -218,6 +218,44 @@ def test_render_orders_enumerate_near_equal_depths(orc):
                 T *= 1 - a[k]
             want.add(tuple(np.round(C, 12)))
         got = {tuple(np.round(c, 12)) for c in alt[0, :n_alt[0]]}
+        assert got == want
+
+
+def test_render_alternatives_branch_on_near_threshold_decisions(orc):
+    """A fragment whose alpha sits 1e-7 (relative) above alpha_min may be blended or not, and a
+    blend that takes T to within 1e-6 of T_min may stop the pixel or not: both colours are valid,
+    each in closed form; the same cases 1% away from the thresholds have one colour."""
+    cam = synth.camera(17, 17, time=0.5)      # principal point (8.5, 8.5): pixel (8, 8)'s centre
+    px = 8 * 17 + 8
+    C = orc.P
+    # one Gaussian facing the camera, centred on the pixel centre (q = 0): alpha = o_t
+    for rel, want_n in ((1e-7, 2), (1e-2, 1)):
+        ot = (1 / 255) * (1 + rel)
+        g = _one([0, 0, 3.0, 0.5], np.log([0.3, 0.3, 0.3, 1e6]), [1, 0, 0, 0], [1, 0, 0, 0],
+                 opacity=math.log(ot / (1 - ot)), rgb=(0.2, 0.5, 0.9))
+        P = orc.project(g, cam)
+        a = P[0, C["ot"]] * math.exp(-0.5 * _q(P[0], 8.5, 8.5))
+        alt, n_alt = orc.render_alternatives(P, cam, [px], 1e-4, 2e-6, 1e-6)
+        assert a == pytest.approx(ot, rel=1e-12)
+        assert n_alt[0] == want_n
+        want = {tuple(np.round(a * np.array([0.2, 0.5, 0.9]), 12))} | ({(0.0, 0.0, 0.0)} if want_n == 2 else set())
+        assert {tuple(np.round(c, 12)) for c in alt[0, :want_n]} == want
+    # a stack of alpha-0.9 Gaussians: T = 0.1, 0.01, 1e-3, 1e-4 (1 + rel) after the fourth
+    for rel, want_n in ((1e-6, 2), (1e-2, 1)):
+        T4 = 1e-4 * (1 + rel)
+        al = 1 - T4 ** 0.25
+        gs = [_one([0, 0, 3.0 + 0.01 * k, 0.5], np.log([0.3, 0.3, 0.3, 1e6]), [1, 0, 0, 0], [1, 0, 0, 0],
+                   opacity=math.log(al / (1 - al)), rgb=(1.0, 1.0, 1.0)) for k in range(4)]
+        g = {k: (np.concatenate([x[k] for x in gs]) if isinstance(gs[0][k], np.ndarray) else gs[0][k]) for k in gs[0]}
+        P = orc.project(g, cam)
+        alt, n_alt = orc.render_alternatives(P, cam, [px], 1e-4, 2e-6, 1e-6)
+        assert n_alt[0] == want_n
+        ak = [P[k, C["ot"]] * math.exp(-0.5 * _q(P[k], 8.5, 8.5)) for k in range(4)]
+        T3 = np.prod([1 - x for x in ak[:3]])
+        full = 1 - T3 * (1 - ak[3])           # white: C = 1 - T after four blends
+        stopped = 1 - T3                      # the fourth stops the pixel
+        got = sorted(round(c[0], 12) for c in alt[0, :want_n])
+        want = sorted({round(full, 12), round(stopped, 12)}) if want_n == 2 else [round(full if rel > 0 else stopped, 12)]
         assert got == want
 
 
