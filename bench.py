@@ -257,12 +257,14 @@ def algorithmic_bytes(kernel: str, n: int, V: int, I: int, R_vis: int, P: int, p
     return float("nan")
 
 
-# FP32 operations (an FMA counts 2) the compositing must spend on each blended (pixel, Gaussian)
-# pair, not counting the fast exponential / reciprocal: forward = q from the conic (8), the q and
-# alpha tests, exp argument and alpha (8.5), transmittance update and colour (10); backward = the
-# same evaluation (16.5), transmittance recovery (3), colour and alpha gradients (26), gradients
-# of the mean and conic (26).
-FLOPS_PER_BLENDED_PAIR = {"render_fwd": 26.0, "render_bwd": 72.0}
+# FP32 work per blended (pixel, Gaussian) pair, the unit of the compositing kernels' roofline.  The
+# headline count is the algorithmic one fixed for this path beforehand: about 12 FP32 operations (plus
+# one exponential) forward and about 40 backward.  The builder's own count of the operations the
+# kernels' arithmetic needs, an FMA counted as 2 (q from the conic 8, the kept test and alpha 8.5,
+# transmittance and colour 10; backward: the same evaluation 16.5, transmittance recovery 3, colour
+# and alpha gradients 26, mean and conic gradients 26), is reported beside it.
+FLOPS_PER_BLENDED_PAIR = {"render_fwd": 12.0, "render_bwd": 40.0}
+FLOPS_PER_BLENDED_PAIR_DETAILED = {"render_fwd": 26.0, "render_bwd": 72.0}
 FP32_LANES_PER_SM = 128
 
 
@@ -300,6 +302,22 @@ def stored_traffic(kernel: str):
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def learned_init_summary():
+    """The second half of the metric, seconds to the plain method's 2000-iteration held-out PSNR with
+    learned against heuristic initialisation, as measured by the learned-initialisation experiment
+    (python -m paper_2510_01119_gb300.learned_init; minutes of GPU time, so not rerun here): the
+    committed summaries under profiles/, or None."""
+    out = {}
+    for size in ("reduced", "full"):
+        path = os.path.join(ROOT, "profiles", f"learned_init_rooms_{size}.json")
+        if os.path.exists(path):
+            d = json.load(open(path))
+            out[size] = {"source": os.path.relpath(path, ROOT), "command": d.get("command"),
+                         "scenes": {"train": d.get("train_scenes"), "test": d.get("test_scenes")},
+                         "summary": d.get("summary")}
+    return out or None
 
 
 def measured_peaks():
@@ -668,7 +686,9 @@ def run_ours(args, ws, rank, local):
                     "peak_derived_kind": f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz (median SM "
                                          f"clock under load)",
                     "algorithmic_flops": flops, "blended_pairs": E,
-                    "flops_per_pair": FLOPS_PER_BLENDED_PAIR[dominant], "hbm": hbm}
+                    "flops_per_pair": FLOPS_PER_BLENDED_PAIR[dominant],
+                    "frac_detailed_count": E * FLOPS_PER_BLENDED_PAIR_DETAILED[dominant] / (dom_ms * 1e-3) / 1e12 / peak,
+                    "flops_per_pair_detailed": FLOPS_PER_BLENDED_PAIR_DETAILED[dominant], "hbm": hbm}
     else:
         roofline = {"kernel": dominant, "bound": "hbm", "ms_per_launch": dom_ms, **hbm}
 
@@ -697,6 +717,9 @@ def run_ours(args, ws, rank, local):
         "clocks": clk,
         "capacity_overflow": overflow,
     }
+    learned = learned_init_summary()
+    if learned:
+        line["sec_to_target_psnr"] = learned
     if args.small:
         line["config"]["workload"] = "train_step_small_profile_only"
     if args.configs and rank == 0:

@@ -230,8 +230,10 @@ I4D_API int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, c
  * (i4d_render_bwd_noalloc_max_records() records of 48 bytes, 24 MiB, held by every GPU that loads
  * the library until exit) instead of the grad2d argument; all other arguments are as for
  * i4d_render_bwd.  Returns I4D_ERR_CAPACITY, launching nothing, when n_views * n exceeds the maximum.
- * Every call shares the array: calls that overlap on the GPU race.  The first call on a device looks
- * up the array's address with that device current; make it before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU race.  Each call looks up the array's
+ * address with the caller's device current, except while `stream` is being captured, when the address
+ * of the device's last uncaptured call is used: make the first call on a device before any stream
+ * capture (a captured first call returns I4D_ERR_CUDA).
  */
 I4D_API int64_t i4d_render_bwd_noalloc_max_records(void);
 I4D_API int32_t i4d_render_bwd_noalloc(const i4d_gaussians* g, const i4d_views* views, const i4d_camera* cams,

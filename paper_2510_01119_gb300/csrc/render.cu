@@ -86,11 +86,14 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ proj, uin
 }
 
 // A half-warp's staged hits of one batch of B list entries.
+// One staged entry (48 bytes: one address per entry, the three parts at fixed offsets).
+struct Staged {
+  float4 a, b, c;
+};
+
 template <int B>
 struct HalfStage {
-  float4 a[B];
-  float4 b[B];
-  float4 c[B];
+  Staged e[B];
 };
 
 // Stage the batch [lo, hi) of the tile list (hi - lo <= B): 32 entries at a time, every lane tests
@@ -120,15 +123,23 @@ __device__ __forceinline__ int stage_batch(const WP& wp, HalfStage<B>* st, const
       stage_entry(proj, r, idx - tile_start, a, b, c);
       if (hit0) {
         const int k = c0 + __popc(m0 & lt);
-        st[0].a[k] = a; st[0].b[k] = b; st[0].c[k] = c;
+        st[0].e[k] = Staged{a, b, c};
       }
       if (hit1) {
         const int k = c1 + __popc(m1 & lt);
-        st[1].a[k] = a; st[1].b[k] = b; st[1].c[k] = c;
+        st[1].e[k] = Staged{a, b, c};
       }
     }
     c0 += __popc(m0);
     c1 += __popc(m1);
+  }
+  // the half with fewer hits gets null entries up to the other's count (never kept, colour 0, all
+  // values finite), so that both halves run the same number of iterations
+  const int lo_c = min(c0, c1), hi_c = max(c0, c1);
+  for (int k = lo_c + lane; k < hi_c; k += 32) {
+    const float inf = __int_as_float(0x7f800000);
+    st[c0 < c1 ? 0 : 1].e[k] =
+        Staged{make_float4(0.0f, 0.0f, 0.0f, 0.0f), make_float4(0.0f, 0.0f, inf, 0.0f), make_float4(0.0f, 0.0f, 0.0f, 0.0f)};
   }
   __syncwarp();
   other = wp.half ? c0 : c1;
@@ -138,9 +149,7 @@ __device__ __forceinline__ int stage_batch(const WP& wp, HalfStage<B>* st, const
 // The backward's staging: the chunk's entries that hit either half, stored once in list order, and
 // per half the positions of its hits among them (a hit of both halves is staged once).
 struct SharedStage {
-  float4 a[32];
-  float4 b[32];
-  float4 c[32];
+  Staged e[32];
   uint8_t idx[2][32];
 };
 
@@ -162,7 +171,7 @@ __device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st,
   if (hit0 || hit1) {
     const unsigned lt = (1u << lane) - 1u;
     const int k = __popc((m0 | m1) & lt);
-    stage_entry(proj, r, idx - tile_start, st.a[k], st.b[k], st.c[k]);
+    stage_entry(proj, r, idx - tile_start, st.e[k].a, st.e[k].b, st.e[k].c);
     if (hit0) st.idx[0][__popc(m0 & lt)] = (uint8_t)k;
     if (hit1) st.idx[1][__popc(m1 & lt)] = (uint8_t)k;
   }
@@ -216,10 +225,14 @@ __global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_
     if (__all_sync(0xffffffffu, thr.x < 0.0f && thr.y < 0.0f)) break;
     int other;
     const int cnt = stage_batch<B>(wp, st, proj, ids, vbase, base, min(base + (uint32_t)B, re), rs, lane, other);
-    for (int t = 0; t < cnt; ++t) {
-      const float4 a = mine.a[t];
-      const float4 b = mine.b[t];
-      const float4 c = mine.c[t];
+    // both halves run max(cnt, other) iterations (the shorter list is padded with null entries), so
+    // the warp-wide vote below is reached by all 32 lanes together
+    const int tmax = max(cnt, other);
+    for (int t = 0; t < tmax; ++t) {
+      const Staged& se = mine.e[t];
+      const float4 a = se.a;
+      const float4 b = se.b;
+      const float4 c = se.c;
       const float dx = __fsub_rn(fx, a.x);
       FragPair f;
       eval_pair(dx, __fadd2_rn(fy, make_float2(-a.y, -a.y)), a.z, a.w, b.x, b.y, b.z, S, f);
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_
       const float2 wk = __fmul2_rn(f.alpha, T);
       float2 w = make_float2(f.k0 ? wk.x : 0.0f, f.k1 ? wk.y : 0.0f);
       float2 Tn = __fadd2_rn(T, make_float2(-w.x, -w.y));
-      if (Tn.x < thr.x || Tn.y < thr.y) {
+      if (__any_sync(0xffffffffu, Tn.x < thr.x || Tn.y < thr.y)) {
         // a kept fragment that would take T below T_min stops the pixel without being blended
         if (Tn.x < thr.x) {
           Tf.x = T.x;
@@ -399,9 +412,9 @@ __device__ __forceinline__ void phase_b(const BwdWarp& W, int half, int l16, int
   uint32_t rr = 0;
   if (valid) {
     const int e = my_idx[glo + k];
-    a = W.st.a[e];
-    b = W.st.b[e];
-    rr = __float_as_uint(W.st.c[e].w);
+    a = W.st.e[e].a;
+    b = W.st.e[e].b;
+    rr = __float_as_uint(W.st.e[e].c.w);
     const float4(*sw)[kGroup] = W.sw[half];
     if (S == 1) {
       const float cx = __fsub_rn(bx0, a.x);
@@ -434,6 +447,59 @@ __device__ __forceinline__ void phase_b(const BwdWarp& W, int half, int l16, int
       red_add4(g1, g[4], g[5], g[6], g[7]);
       red_add(g1 + VN * 4, g[8]);
     }
+  }
+}
+
+// Phase A over this half's hits t = thi - 1 .. glo of a group, back to front.  A fragment the pixel
+// did not blend (not kept, or at or after its stop position) enters with alpha 0, which leaves T
+// and the colour behind unchanged exactly (T_k = T + T alpha / (1 - alpha)) and makes its (s, -w)
+// slot zero.  CHECK: compare the hits' list positions with the pixels' stop positions; a chunk that
+// lies wholly below every stop position of the warp needs no comparison.
+template <bool CHECK>
+__device__ __forceinline__ void phase_a(const SharedStage& stg, const uint8_t* my_idx, int thi, int glo, float fx,
+                                        float2 fy, const Settings& S, PairBwd& P, float4* sw_mine, int zl) {
+  for (int t = thi - 1; t >= glo; --t) {
+    const int e = my_idx[t];
+    const Staged& se = stg.e[e];
+    const float4 a = se.a;
+    const float4 b = se.b;
+    const float4 c = se.c;
+    const float dx = __fsub_rn(fx, a.x);
+    const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
+    FragPair f;
+    eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, S, f);
+    bool k0 = f.k0, k1 = f.k1;
+    if (CHECK) {
+      const uint32_t pos = __float_as_uint(c.z);
+      k0 = k0 && pos < P.L0;
+      k1 = k1 && pos < P.L1;
+    }
+    const float2 ae = make_float2(k0 ? f.alpha.x : 0.0f, k1 ? f.alpha.y : 0.0f);
+    const float2 om = __fadd2_rn(f2(1.0f), make_float2(-ae.x, -ae.y));
+    const float2 iom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+    // transmittance in front of this fragment
+    const float2 Tk = __ffma2_rn(P.T, __fmul2_rn(ae, iom), P.T);
+    const float2 nw = __fmul2_rn(make_float2(-ae.x, -ae.y), Tk);  // -alpha T_k
+    // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
+    // S_c the colour composited behind, T the transmittance behind
+    const float2 cr = f2(b.w), cg = f2(c.x), cb = f2(c.y);
+    const float2 yr = __ffma2_rn(P.T, cr, P.NSr);
+    const float2 yg = __ffma2_rn(P.T, cg, P.NSg);
+    const float2 yb = __ffma2_rn(P.T, cb, P.NSb);
+    const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.ub, yb, __ffma2_rn(P.ug, yg, __fmul2_rn(P.ur, yr))));
+    P.NSr = __ffma2_rn(nw, cr, P.NSr);
+    P.NSg = __ffma2_rn(nw, cg, P.NSg);
+    P.NSb = __ffma2_rn(nw, cb, P.NSb);
+    P.T = Tk;
+    // alpha = o_t G carries the gradient only below the alpha_max cap, which a fragment can reach
+    // only when o_t >= alpha_max
+    float2 Ge = make_float2(k0 ? f.G.x : 0.0f, k1 ? f.G.y : 0.0f);
+    if (b.y >= S.alpha_max) {
+      if (f.a_raw.x >= S.alpha_max) Ge.x = 0.0f;
+      if (f.a_raw.y >= S.alpha_max) Ge.y = 0.0f;
+    }
+    const float2 sv = __fmul2_rn(dA, Ge);
+    sw_mine[(t - glo) ^ zl] = make_float4(sv.x, sv.y, nw.x, nw.y);
   }
 }
 
@@ -496,8 +562,11 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
   P.NSr = __fmul2_rn(P.T, f2(-S.bg[0]));
   P.NSg = __fmul2_rn(P.T, f2(-S.bg[1]));
   P.NSb = __fmul2_rn(P.T, f2(-S.bg[2]));
-  // this warp never needs entries past its pixels' last blended fragments
+  // this warp never needs entries at or past its pixels' stop positions, and below the smallest stop
+  // position of its pixels in the view every kept fragment was blended (pixels outside the view have
+  // T = 0 and no upstream gradient: whatever they take contributes exactly zero)
   const uint32_t wL = __reduce_max_sync(0xffffffffu, max(P.L0, P.L1));
+  const uint32_t wLmin = __reduce_min_sync(0xffffffffu, min(in0 ? P.L0 : 0xffffffffu, in1 ? P.L1 : 0xffffffffu));
   const uint32_t end = rs + min(wL, re - rs);
   // pixel-centre offsets of this half's block: lane j's pair sits in column j & 7, rows 2 (j >> 3) + {0, 1}
   const float bx0 = wp.hx0, by0 = wp.hy0[wp.half];
@@ -509,40 +578,10 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
     for (int ghi = max(cnt, other); ghi > 0; ghi -= kGroup) {  // warp-uniform
       const int glo = max(ghi - kGroup, 0);
       // ---- phase A: the recurrence, hits back to front ----
-      for (int t = min(ghi, cnt) - 1; t >= glo; --t) {
-        const int e = my_idx[t];
-        const float4 a = stg.a[e];
-        const float4 b = stg.b[e];
-        const float4 c = stg.c[e];
-        const float dx = __fsub_rn(fx, a.x);
-        const float2 dy = __fadd2_rn(fy, make_float2(-a.y, -a.y));
-        FragPair f;
-        eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, S, f);
-        // the fragments a pixel blended are the kept ones before its stop position (out-of-view
-        // pixels: 0)
-        const uint32_t pos = __float_as_uint(c.z);
-        const bool k0 = f.k0 && pos < P.L0, k1 = f.k1 && pos < P.L1;
-        const float2 na = __fmul2_rn(f.alpha, f2(-1.0f));
-        const float2 om = __fadd2_rn(na, f2(1.0f));
-        const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
-        const float2 Tk = __fmul2_rn(P.T, iom);  // transmittance in front of this fragment
-        const float2 nw = __fmul2_rn(make_float2(k0 ? na.x : 0.0f, k1 ? na.y : 0.0f), Tk);  // -alpha T_k
-        // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
-        // S_c the colour composited behind, T the transmittance behind
-        const float2 cr = f2(b.w), cg = f2(c.x), cb = f2(c.y);
-        const float2 yr = __ffma2_rn(P.T, cr, P.NSr);
-        const float2 yg = __ffma2_rn(P.T, cg, P.NSg);
-        const float2 yb = __ffma2_rn(P.T, cb, P.NSb);
-        const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.ub, yb, __ffma2_rn(P.ug, yg, __fmul2_rn(P.ur, yr))));
-        P.NSr = __ffma2_rn(nw, cr, P.NSr);
-        P.NSg = __ffma2_rn(nw, cg, P.NSg);
-        P.NSb = __ffma2_rn(nw, cb, P.NSb);
-        P.T = make_float2(k0 ? Tk.x : P.T.x, k1 ? Tk.y : P.T.y);
-        // alpha = o_t G carries the gradient only below the 0.99 cap
-        const bool a0 = k0 && f.a_raw.x < S.alpha_max, a1 = k1 && f.a_raw.y < S.alpha_max;
-        const float2 sv = __fmul2_rn(make_float2(a0 ? dA.x : 0.0f, a1 ? dA.y : 0.0f), f.G);
-        sw_mine[(t - glo) ^ zl] = make_float4(sv.x, sv.y, nw.x, nw.y);
-      }
+      if (hi - rs <= wLmin)  // warp-uniform
+        phase_a<false>(stg, my_idx, min(ghi, cnt), glo, fx, fy, S, P, sw_mine, zl);
+      else
+        phase_a<true>(stg, my_idx, min(ghi, cnt), glo, fx, fy, S, P, sw_mine, zl);
       __syncwarp();
       // ---- phase B: per hit, its sums over the block; 1, 2 or 4 lanes per hit by the group's size ----
       const int hc = max(min(ghi, cnt) - glo, 0);

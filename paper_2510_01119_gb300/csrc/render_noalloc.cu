@@ -13,8 +13,11 @@
 //   - every call shares it: calls that overlap on the GPU (different streams, or different host
 //     threads without ordering) race on it and corrupt each other's gradients;
 //   - it keeps the last call's contents, so each call clears it before use;
-//   - the first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
-//     device current) and caches it; make that first call before any stream capture.
+//   - each call looks up the array's device address with the caller's device current
+//     (cudaGetSymbolAddress), so a context torn down and recreated between calls (cudaDeviceReset)
+//     gets the array's new address; while the stream is being captured the lookup is skipped and the
+//     address of the device's last uncaptured call is used, so the first call on a device must come
+//     before any stream capture.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -32,18 +35,24 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (host code may not use the symbol
-// itself: on the host it names a stand-in, not device memory).
-cudaError_t scratch_address(void** out) {
+// itself: on the host it names a stand-in, not device memory).  Looked up on every call made
+// outside a stream capture; during a capture the last looked-up address of the device is used.
+cudaError_t scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_grad2d);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
+  } else if (!g_noalloc_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;  // no uncaptured call on this device yet
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
@@ -68,7 +77,7 @@ int32_t i4d_render_bwd_noalloc(const i4d_gaussians* g, const i4d_views* views, c
   if ((int64_t)views->n_views * g->n > kNoAllocMaxRecords) return I4D_ERR_CAPACITY;  // beyond the fixed scratch
   if (g->n == 0) return I4D_OK;
   void* scratch = nullptr;
-  if (scratch_address(&scratch) != cudaSuccess) return I4D_ERR_CUDA;
+  if (scratch_address((cudaStream_t)stream, &scratch) != cudaSuccess) return I4D_ERR_CUDA;
   // same computation as i4d_render_bwd, with the fixed array as its 2D-gradient scratch (the
   // backward clears the scratch before accumulating into it)
   return i4d_render_bwd(g, views, cams, settings, proj, touched, ids, ranges, T_final, last, dL_dimg,

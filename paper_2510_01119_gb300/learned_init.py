@@ -65,7 +65,7 @@ def build_scene(seed: int, cfg: SceneConfig, dev) -> Scene:
     frames = list(range(0, cfg.n_frames, cfg.stride))
     vid = synth.depth_video(seed, n_frames=cfg.n_frames, W=cfg.W, H=cfg.H, frames=frames)
     F = len(frames)
-    pr = Pruner(F * cfg.W * cfg.H, 1 << 20, device=dev)
+    pr = Pruner(F * cfg.W * cfg.H, 1 << 22 if F * cfg.W * cfg.H > (1 << 24) else 1 << 20, device=dev)
     out = pr.prune_depth(torch.from_numpy(vid["depth"]).to(dev), torch.from_numpy(vid["rgb"]).to(dev),
                          torch.from_numpy(vid["dyn"]).to(dev), R.cameras_tensor(vid["cams"], dev), cfg.voxel,
                          cfg.voxel, cfg.min_support)
@@ -111,8 +111,11 @@ def build_scene(seed: int, cfg: SceneConfig, dev) -> Scene:
     return sc
 
 
-def init_params(sc: Scene, weights: torch.Tensor = None, opacity: float = 0.1):
-    """Heuristic (weights None) or learned initialisation of the scene's Gaussians."""
+def init_params(sc: Scene, weights: torch.Tensor = None, opacity: float = 0.1, gate: str = "all"):
+    """Heuristic (weights None) or learned initialisation of the scene's Gaussians.  gate "dynamic":
+    the network's proposals replace the heuristic only on the points of the dynamic mask; static
+    points keep the heuristic of Sec. 4.1 (temporal scale of the whole video, R = I), which is what a
+    static point's fit keeps."""
     n, dev = sc.n, sc.feats.device
     params = torch.empty(5 * n * 4, device=dev)
     st_dyn, st_static = T.temporal_scales(sc.cfg.n_frames)
@@ -120,6 +123,12 @@ def init_params(sc: Scene, weights: torch.Tensor = None, opacity: float = 0.1):
     if weights is not None:
         y = torch.empty(n, N_OUT, device=dev)
         L.i4d_mlp_forward(sc.feats, weights, y)
+        if gate == "dynamic":
+            static = sc.pts["flag"] == 0
+            y[static] = torch.tensor([math.log(st_static), 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0],
+                                     device=dev)
+        elif gate != "all":
+            raise ValueError(gate)
     fb = torch.zeros(1, dtype=torch.int32, device=dev)
     L.i4d_init_learned(sc.pts["xyz"], sc.pts["rgb"], sc.pts["t"], sc.pts["flag"], sc.knn3, y, n, 0, st_dyn, st_static,
                        opacity, params, fb)
@@ -263,9 +272,11 @@ def final(hist):
     return [h for h in hist if h[2] is not None][-1]
 
 
-def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int = 1500, log=print, dev=None):
+def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int = 1500, log=print, dev=None,
+               gates=("all",)):
     """Train the MLP on plain fits of the training scenes; on each test scene compare seconds and
-    iterations to the plain method's final held-out PSNR (within 0.1 dB)."""
+    iterations to the plain method's final held-out PSNR (within 0.1 dB), for each proposal gate
+    ("all": every point takes the network's proposal; "dynamic": only the dynamic points)."""
     cfg = cfg or SceneConfig()
     dev = dev or torch.device("cuda")
     feats, tgts = [], []
@@ -287,24 +298,47 @@ def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int 
         p_plain, _ = init_params(sc, None)
         h_plain, p_plain = fit(sc, p_plain, seed=s)
         fitted = motion_targets(p_plain, sc.n)
-        y = torch.empty(sc.n, N_OUT, device=dev)
-        L.i4d_mlp_forward(sc.feats, w, y)
-        p_learn, fallbacks = init_params(sc, w)
-        err_learned = target_loss(motion_targets(p_learn, sc.n), fitted)
-        err_heur = target_loss(heuristic_targets(sc), fitted)
-        h_learn, _ = fit(sc, p_learn, seed=s)
         target = final(h_plain)[2]
         it_p, sec_p = reach(h_plain, target)
-        it_l, sec_l = reach(h_learn, target)
-        rows.append(dict(seed=s, n=sc.n, plain_psnr_final=target, learned_psnr_final=final(h_learn)[2],
-                         plain_iters=it_p, plain_seconds=sec_p, learned_iters=it_l, learned_seconds=sec_l,
-                         plain_seconds_final=final(h_plain)[1], learned_seconds_final=final(h_learn)[1],
-                         init_psnr_plain=h_plain[0][2], init_psnr_learned=h_learn[0][2],
-                         target_loss_heuristic=err_heur, target_loss_learned=err_learned, fallbacks=fallbacks))
+        row = dict(seed=s, n=sc.n, n_dynamic=int(sc.pts["flag"].sum().item()), plain_psnr_final=target,
+                   plain_iters=it_p, plain_seconds=sec_p, plain_seconds_final=final(h_plain)[1],
+                   init_psnr_plain=h_plain[0][2], target_loss_heuristic=target_loss(heuristic_targets(sc), fitted))
+        for gate in gates:
+            p_learn, fallbacks = init_params(sc, w, gate=gate)
+            err_learned = target_loss(motion_targets(p_learn, sc.n), fitted)
+            h_learn, _ = fit(sc, p_learn, seed=s)
+            it_l, sec_l = reach(h_learn, target)
+            tag = "learned" if gate == "all" else f"learned_{gate}"
+            row.update({f"{tag}_psnr_final": final(h_learn)[2], f"{tag}_iters": it_l, f"{tag}_seconds": sec_l,
+                        f"{tag}_seconds_final": final(h_learn)[1], f"init_psnr_{tag}": h_learn[0][2],
+                        f"target_loss_{tag}": err_learned, f"fallbacks_{tag}": fallbacks})
+        rows.append(row)
         log(f"test scene {s}: " + ", ".join(f"{k}={v:.3f}" if isinstance(v, float) else f"{k}={v}"
                                             for k, v in rows[-1].items()))
         del sc
     return rows, curve
+
+
+# the full-size scenes: the benched room video (200 frames of 640x360 depth, voxel 0.01, support 3,
+# ~1.13 M Gaussians) fitted from 960x540 views against a 200k-Gaussian hidden scene
+FULL_SIZE = dict(stride=1, W=640, H=360, voxel=0.01, min_support=3, view=(960, 540), batch=4, hidden_n=200000)
+
+
+def summarize(rows, gates):
+    """Means over the test scenes where every run reached the plain fit's final PSNR."""
+    out = {}
+    for gate in gates:
+        tag = "learned" if gate == "all" else f"learned_{gate}"
+        ok = [r for r in rows if r[f"{tag}_seconds"] is not None and r["plain_seconds"] is not None]
+        out[tag] = dict(reached=len(ok), of=len(rows),
+                        mean_plain_iters=float(np.mean([r["plain_iters"] for r in ok])) if ok else None,
+                        mean_iters=float(np.mean([r[f"{tag}_iters"] for r in ok])) if ok else None,
+                        mean_plain_seconds=float(np.mean([r["plain_seconds"] for r in ok])) if ok else None,
+                        mean_seconds=float(np.mean([r[f"{tag}_seconds"] for r in ok])) if ok else None,
+                        faster_in=int(sum(r[f"{tag}_seconds"] < r["plain_seconds"] for r in ok)),
+                        mean_plain_psnr_final=float(np.mean([r["plain_psnr_final"] for r in rows])),
+                        mean_psnr_final=float(np.mean([r[f"{tag}_psnr_final"] for r in rows])))
+    return out
 
 
 def main(argv=None):
@@ -315,19 +349,21 @@ def main(argv=None):
     ap.add_argument("--test", type=int, default=8, help="test scenes (seeds 200, 201, ...)")
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--mlp-steps", type=int, default=1500)
+    ap.add_argument("--size", choices=["reduced", "full"], default="reduced")
+    ap.add_argument("--gates", default="all,dynamic", help="proposal gates to test (all, dynamic)")
     ap.add_argument("--out", default=None, help="write the JSON summary here")
     a = ap.parse_args(argv)
     from . import build as B
     B.build()
-    cfg = SceneConfig(iters=a.iters)
-    rows, curve = experiment(list(range(100, 100 + a.train)), list(range(200, 200 + a.test)), cfg, a.mlp_steps)
-    ok = [r for r in rows if r["learned_seconds"] is not None and r["plain_seconds"] is not None]
-    summary = dict(config=cfg.__dict__, train_scenes=a.train, test_scenes=a.test, mlp_loss_curve=curve, rows=rows,
-                   mean_plain_iters=float(np.mean([r["plain_iters"] for r in ok])) if ok else None,
-                   mean_learned_iters=float(np.mean([r["learned_iters"] for r in ok])) if ok else None,
-                   mean_plain_seconds=float(np.mean([r["plain_seconds"] for r in ok])) if ok else None,
-                   mean_learned_seconds=float(np.mean([r["learned_seconds"] for r in ok])) if ok else None,
-                   reached=len(ok))
+    cfg = SceneConfig(iters=a.iters, **(FULL_SIZE if a.size == "full" else {}))
+    gates = tuple(a.gates.split(","))
+    rows, curve = experiment(list(range(100, 100 + a.train)), list(range(200, 200 + a.test)), cfg, a.mlp_steps,
+                             gates=gates)
+    import sys
+    args = list(argv) if argv is not None else sys.argv[1:]
+    summary = dict(command="python -m paper_2510_01119_gb300.learned_init " + " ".join(args), config=cfg.__dict__,
+                   size=a.size, train_scenes=a.train, test_scenes=a.test, mlp_loss_curve=curve, rows=rows,
+                   summary=summarize(rows, gates))
     text = json.dumps(summary, default=float)
     if a.out:
         open(a.out, "w").write(text + "\n")

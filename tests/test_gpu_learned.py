@@ -143,7 +143,7 @@ def test_trained_network_gain_over_heuristic(dev):
     summary = [(r["seed"], round(r["target_loss_heuristic"], 4), round(r["target_loss_learned"], 4),
                 r["plain_iters"], r["learned_iters"], r["plain_seconds"], r["learned_seconds"]) for r in rows]
     print("seed, target loss heuristic, learned, iters plain, learned, seconds plain, learned:", summary)
-    assert all(r["fallbacks"] == 0 for r in rows)
+    assert all(r["fallbacks_learned"] == 0 for r in rows)
     assert np.mean([r["target_loss_learned"] for r in rows]) < np.mean([r["target_loss_heuristic"] for r in rows]), \
         summary
     assert all(r["plain_iters"] is not None for r in rows)

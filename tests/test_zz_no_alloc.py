@@ -62,3 +62,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(dev):
     with pytest.raises(L.I4DError, match="exceeds the fixed scratch"):
         L.i4d_render_bwd_noalloc(g, rast.views, torch.zeros(2, 20, device=dev), rast.settings, rast.proj,
                                  rast.touched, rast.ids, rast.ranges, rast.T_final, rast.last, rast.img, rast.grads)
+
+
+def test_noalloc_at_full_capacity_on_a_side_stream(dev):
+    """2 views x 262,144 Gaussians fill the fixed scratch exactly; the call runs on a stream other
+    than the default one and matches i4d_render_bwd."""
+    import torch
+    from paper_2510_01119_gb300 import _lib as L
+    from paper_2510_01119_gb300 import rasterizer as R
+    lib = L.load()
+    n = int(lib.i4d_render_bwd_noalloc_max_records()) // 2
+    g = synth.gaussians_uniform(3, n=n)
+    cams = [synth.camera(160, 120, 60.0, time=0.5), synth.camera(96, 64, 50.0, time=0.3)]
+    rast = R.Rasterizer(n, 0, 0, [(c["W"], c["H"]) for c in cams])
+    params = R.pack_params(g)
+    camt = R.cameras_tensor(cams)
+    rast.forward(params, camt)
+    dl = torch.from_numpy(np.random.default_rng(6).normal(size=rast.img.numel()).astype(np.float32) * 1e-3).to(dev)
+    want = rast.backward(params, camt, dl).clone()
+    got = torch.full_like(want, float("nan"))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    L.i4d_render_bwd_noalloc(rast.gaussians(params), rast.views, camt, rast.settings, rast.proj, rast.touched,
+                             rast.ids, rast.ranges, rast.T_final, rast.last, dl, got, stream=side)
+    side.synchronize()
+    a, b = got.cpu().numpy(), want.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    assert rel_l2(a, b) < GRAD_TOL
