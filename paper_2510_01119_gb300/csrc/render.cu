@@ -71,6 +71,25 @@ struct WarpPix {
   __device__ __forceinline__ bool misses(const float4 b, int h) const {
     return b.y < hx0 || b.x > hx1 || b.w < hy0[h] || b.z > hy1[h];
   }
+  // Whether a staged record (a = (u, v, sa, sb2), b = (sc, o_t, m_thr, r)) can be kept at some pixel
+  // centre of half h's block: the largest exponent m = sa dx^2 + sb2 dx dy + sc dy^2 over the block's
+  // rectangle of pixel centres reaches m_thr.  m is concave, so its maximum over the rectangle is 0
+  // at the projected mean when that lies inside, else it lies on one of the (at most two) edges facing
+  // the mean, where m is a 1D quadratic maximised at its stationary point clamped to the edge.  The
+  // test keeps a slack of 1e-4 (relative and absolute) so that rounding never drops a pixel the
+  // per-pixel test keeps.
+  __device__ __forceinline__ bool meets(const float4 a, const float4 b, int h) const {
+    const float u = a.x, v = a.y, sa = a.z, sb2 = a.w, sc = b.x, mthr = b.z;
+    const float y0 = hy0[h], y1 = hy1[h];
+    const float dxc = fminf(fmaxf(u, hx0), hx1) - u;
+    const float dyc = fminf(fmaxf(v, y0), y1) - v;
+    const float dy1 = fminf(fmaxf(v - __fdividef(0.5f * sb2, sc) * dxc, y0), y1) - v;
+    const float dx2 = fminf(fmaxf(u - __fdividef(0.5f * sb2, sa) * dyc, hx0), hx1) - u;
+    const float m1 = dxc != 0.0f ? fmaf(sa * dxc, dxc, fmaf(sb2 * dxc, dy1, sc * dy1 * dy1)) : -INFINITY;
+    const float m2 = dyc != 0.0f ? fmaf(sa * dx2, dx2, fmaf(sb2 * dx2, dyc, sc * dyc * dyc)) : -INFINITY;
+    const float m = (dxc == 0.0f && dyc == 0.0f) ? 0.0f : fmaxf(m1, m2);
+    return m >= mthr - (1e-4f * fabsf(mthr) + 1e-4f);
+  }
 };
 
 // The staged form of a record (slice_project writes it ready: 64 bytes, the box first): a = (u, v,
@@ -160,18 +179,24 @@ __device__ __forceinline__ int stage_chunk_shared(const WP& wp, SharedStage& st,
   const uint32_t idx = lo + lane;
   uint32_t r = 0;
   bool hit0 = false, hit1 = false;
+  float4 a, b, c;
   if (idx < hi) {
     r = vbase + __ldg(&ids[idx]);
     const float4 box = __ldg(&proj[4 * (size_t)r]);
     hit0 = !wp.misses(box, 0);
     hit1 = !wp.misses(box, 1);
+    if (hit0 || hit1) {
+      stage_entry(proj, r, idx - tile_start, a, b, c);
+      hit0 = hit0 && wp.meets(a, b, 0);
+      hit1 = hit1 && wp.meets(a, b, 1);
+    }
   }
   const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
   const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
   if (hit0 || hit1) {
     const unsigned lt = (1u << lane) - 1u;
     const int k = __popc((m0 | m1) & lt);
-    stage_entry(proj, r, idx - tile_start, st.e[k].a, st.e[k].b, st.e[k].c);
+    st.e[k] = Staged{a, b, c};
     if (hit0) st.idx[0][__popc(m0 & lt)] = (uint8_t)k;
     if (hit1) st.idx[1][__popc(m1 & lt)] = (uint8_t)k;
   }

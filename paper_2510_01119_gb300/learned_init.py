@@ -123,10 +123,22 @@ def init_params(sc: Scene, weights: torch.Tensor = None, opacity: float = 0.1, g
     if weights is not None:
         y = torch.empty(n, N_OUT, device=dev)
         L.i4d_mlp_forward(sc.feats, weights, y)
+        heur = torch.zeros_like(y)
+        heur[:, 0] = torch.where(sc.pts["flag"] != 0, math.log(st_dyn), math.log(st_static))
+        heur[:, 4] = heur[:, 8] = 1.0
         if gate == "dynamic":
             static = sc.pts["flag"] == 0
-            y[static] = torch.tensor([math.log(st_static), 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0],
-                                     device=dev)
+            y[static] = heur[static]
+        elif gate == "st":          # the temporal scale from the network, the rotation of the heuristic
+            y[:, 4:] = heur[:, 4:]
+        elif gate == "half":        # halfway between the heuristic and the proposal (normalised quaternions)
+            ql = y[:, 4:8] / y[:, 4:8].norm(dim=1, keepdim=True).clamp_min(1e-12)
+            qr = y[:, 8:12] / y[:, 8:12].norm(dim=1, keepdim=True).clamp_min(1e-12)
+            ql = ql * torch.where(ql[:, :1] < 0, -1.0, 1.0)
+            qr = qr * torch.where(qr[:, :1] < 0, -1.0, 1.0)
+            y = 0.5 * (y + heur)
+            y[:, 4:8] = 0.5 * (ql + heur[:, 4:8])
+            y[:, 8:12] = 0.5 * (qr + heur[:, 8:12])
         elif gate != "all":
             raise ValueError(gate)
     fb = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -149,8 +161,10 @@ class Evaluator:
         return float(self.out.item())
 
 
-def fit(sc: Scene, params: torch.Tensor, iters: int = None, eval_every: int = None, seed: int = 0):
-    """Train with the plain step; returns (history [(iteration, train seconds, held-out PSNR)], params)."""
+def fit(sc: Scene, params: torch.Tensor, iters: int = None, eval_every: int = None, seed: int = 0,
+        snapshot_at: int = None):
+    """Train with the plain step; returns (history [(iteration, train seconds, held-out PSNR)], params),
+    and with snapshot_at also the motion values (motion_targets) at that iteration."""
     cfg = sc.cfg
     iters = cfg.iters if iters is None else iters
     eval_every = cfg.eval_every if eval_every is None else eval_every
@@ -191,8 +205,12 @@ def fit(sc: Scene, params: torch.Tensor, iters: int = None, eval_every: int = No
             step.rast._alloc_bins(int(1.5 * int(step.rast.n_inst.item())) + 65536)
             step.capture(warmup=0)
         hist.append((k, train_ms / 1e3, ev.psnr(params)))
+        if snapshot_at is not None and k == snapshot_at:
+            snap = motion_targets(params, sc.n)
     if overflows:
         hist.append(("overflow_chunks", overflows, None))
+    if snapshot_at is not None:
+        return hist, params, snap
     return hist, params
 
 
@@ -273,25 +291,36 @@ def final(hist):
 
 
 def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int = 1500, log=print, dev=None,
-               gates=("all",)):
+               gates=("all",), mid_iter: int = None):
     """Train the MLP on plain fits of the training scenes; on each test scene compare seconds and
     iterations to the plain method's final held-out PSNR (within 0.1 dB), for each proposal gate
-    ("all": every point takes the network's proposal; "dynamic": only the dynamic points)."""
+    ("all": every point takes the network's proposal; "dynamic": only the dynamic points; "st": the
+    temporal scale only; "half": halfway between heuristic and proposal).  With mid_iter, a second
+    network is trained on the plain fits' motion values at that iteration and tested with gate all
+    (tag "learned_mid")."""
     cfg = cfg or SceneConfig()
     dev = dev or torch.device("cuda")
-    feats, tgts = [], []
+    feats, tgts, tgts_mid = [], [], []
     t0 = time.time()
     for s in train_seeds:
         sc = build_scene(s, cfg, dev)
         params, _ = init_params(sc, None)
-        hist, params = fit(sc, params, seed=s)
+        if mid_iter is not None:
+            hist, params, snap = fit(sc, params, seed=s, snapshot_at=mid_iter)
+            tgts_mid.append(snap)
+        else:
+            hist, params = fit(sc, params, seed=s)
         feats.append(sc.feats)
         tgts.append(motion_targets(params, sc.n))
         log(f"train scene {s}: n={sc.n} plain PSNR {final(hist)[2]:.2f} dB ({time.time() - t0:.0f} s)")
         del sc
     F = torch.cat(feats)
-    Tg = torch.cat(tgts)
-    w, curve = train_mlp(F, Tg, steps=mlp_steps, log=log)
+    w, curve = train_mlp(F, torch.cat(tgts), steps=mlp_steps, log=log)
+    nets = [(gate, w, "learned" if gate == "all" else f"learned_{gate}") for gate in gates]
+    if mid_iter is not None:
+        w_mid, _ = train_mlp(F, torch.cat(tgts_mid), steps=mlp_steps, log=log)
+        nets.append(("all", w_mid, "learned_mid"))
+    del F
     rows = []
     for s in test_seeds:
         sc = build_scene(s, cfg, dev)
@@ -302,21 +331,22 @@ def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int 
         it_p, sec_p = reach(h_plain, target)
         row = dict(seed=s, n=sc.n, n_dynamic=int(sc.pts["flag"].sum().item()), plain_psnr_final=target,
                    plain_iters=it_p, plain_seconds=sec_p, plain_seconds_final=final(h_plain)[1],
-                   init_psnr_plain=h_plain[0][2], target_loss_heuristic=target_loss(heuristic_targets(sc), fitted))
-        for gate in gates:
-            p_learn, fallbacks = init_params(sc, w, gate=gate)
+                   init_psnr_plain=h_plain[0][2], target_loss_heuristic=target_loss(heuristic_targets(sc), fitted),
+                   plain_curve=[(h[0], h[2]) for h in h_plain if h[2] is not None])
+        for gate, wt, tag in nets:
+            p_learn, fallbacks = init_params(sc, wt, gate=gate)
             err_learned = target_loss(motion_targets(p_learn, sc.n), fitted)
             h_learn, _ = fit(sc, p_learn, seed=s)
             it_l, sec_l = reach(h_learn, target)
-            tag = "learned" if gate == "all" else f"learned_{gate}"
             row.update({f"{tag}_psnr_final": final(h_learn)[2], f"{tag}_iters": it_l, f"{tag}_seconds": sec_l,
                         f"{tag}_seconds_final": final(h_learn)[1], f"init_psnr_{tag}": h_learn[0][2],
-                        f"target_loss_{tag}": err_learned, f"fallbacks_{tag}": fallbacks})
+                        f"target_loss_{tag}": err_learned, f"fallbacks_{tag}": fallbacks,
+                        f"{tag}_curve": [(h[0], h[2]) for h in h_learn if h[2] is not None]})
         rows.append(row)
         log(f"test scene {s}: " + ", ".join(f"{k}={v:.3f}" if isinstance(v, float) else f"{k}={v}"
-                                            for k, v in rows[-1].items()))
+                                            for k, v in rows[-1].items() if not k.endswith("curve")))
         del sc
-    return rows, curve
+    return rows, curve, [tag for _, _, tag in nets]
 
 
 # the full-size scenes: the benched room video (200 frames of 640x360 depth, voxel 0.01, support 3,
@@ -324,11 +354,10 @@ def experiment(train_seeds, test_seeds, cfg: SceneConfig = None, mlp_steps: int 
 FULL_SIZE = dict(stride=1, W=640, H=360, voxel=0.01, min_support=3, view=(960, 540), batch=4, hidden_n=200000)
 
 
-def summarize(rows, gates):
-    """Means over the test scenes where every run reached the plain fit's final PSNR."""
+def summarize(rows, tags):
+    """Means over the test scenes where each run reached the plain fit's final PSNR."""
     out = {}
-    for gate in gates:
-        tag = "learned" if gate == "all" else f"learned_{gate}"
+    for tag in tags:
         ok = [r for r in rows if r[f"{tag}_seconds"] is not None and r["plain_seconds"] is not None]
         out[tag] = dict(reached=len(ok), of=len(rows),
                         mean_plain_iters=float(np.mean([r["plain_iters"] for r in ok])) if ok else None,
@@ -350,20 +379,22 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--mlp-steps", type=int, default=1500)
     ap.add_argument("--size", choices=["reduced", "full"], default="reduced")
-    ap.add_argument("--gates", default="all,dynamic", help="proposal gates to test (all, dynamic)")
+    ap.add_argument("--gates", default="all,half", help="proposal gates to test (all, dynamic, st, half)")
+    ap.add_argument("--mid-iter", type=int, default=None,
+                    help="also train on the plain fits' motion values at this iteration")
     ap.add_argument("--out", default=None, help="write the JSON summary here")
     a = ap.parse_args(argv)
     from . import build as B
     B.build()
     cfg = SceneConfig(iters=a.iters, **(FULL_SIZE if a.size == "full" else {}))
     gates = tuple(a.gates.split(","))
-    rows, curve = experiment(list(range(100, 100 + a.train)), list(range(200, 200 + a.test)), cfg, a.mlp_steps,
-                             gates=gates)
+    rows, curve, tags = experiment(list(range(100, 100 + a.train)), list(range(200, 200 + a.test)), cfg,
+                                   a.mlp_steps, gates=gates, mid_iter=a.mid_iter)
     import sys
     args = list(argv) if argv is not None else sys.argv[1:]
     summary = dict(command="python -m paper_2510_01119_gb300.learned_init " + " ".join(args), config=cfg.__dict__,
                    size=a.size, train_scenes=a.train, test_scenes=a.test, mlp_loss_curve=curve, rows=rows,
-                   summary=summarize(rows, gates))
+                   summary=summarize(rows, tags))
     text = json.dumps(summary, default=float)
     if a.out:
         open(a.out, "w").write(text + "\n")

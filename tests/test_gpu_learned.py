@@ -138,7 +138,7 @@ def test_trained_network_gain_over_heuristic(dev):
     (a) must improve on the heuristic; (b) is reported as measured, whichever way it goes."""
     from paper_2510_01119_gb300 import learned_init as LI
     cfg = LI.SceneConfig(iters=600, eval_every=50)
-    rows, curve = LI.experiment(list(range(100, 106)), [200, 201], cfg, mlp_steps=800, log=lambda s: None, dev=dev)
+    rows, curve, _ = LI.experiment(list(range(100, 106)), [200, 201], cfg, mlp_steps=800, log=lambda s: None, dev=dev)
     assert curve[-1][1] < 0.5 * curve[0][1]                   # the MLP trained
     summary = [(r["seed"], round(r["target_loss_heuristic"], 4), round(r["target_loss_learned"], 4),
                 r["plain_iters"], r["learned_iters"], r["plain_seconds"], r["learned_seconds"]) for r in rows]
