@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_
     // both halves run max(cnt, other) iterations (the shorter list is padded with null entries), so
     // the warp-wide vote below is reached by all 32 lanes together
     const int tmax = max(cnt, other);
+#pragma unroll 2
     for (int t = 0; t < tmax; ++t) {
       const Staged& se = mine.e[t];
       const float4 a = se.a;
@@ -516,13 +517,9 @@ __device__ __forceinline__ void phase_a(const SharedStage& stg, const uint8_t* m
     P.NSg = __ffma2_rn(nw, cg, P.NSg);
     P.NSb = __ffma2_rn(nw, cb, P.NSb);
     P.T = Tk;
-    // alpha = o_t G carries the gradient only below the alpha_max cap, which a fragment can reach
-    // only when o_t >= alpha_max
-    float2 Ge = make_float2(k0 ? f.G.x : 0.0f, k1 ? f.G.y : 0.0f);
-    if (b.y >= S.alpha_max) {
-      if (f.a_raw.x >= S.alpha_max) Ge.x = 0.0f;
-      if (f.a_raw.y >= S.alpha_max) Ge.y = 0.0f;
-    }
+    // alpha = o_t G carries the gradient only below the alpha_max cap
+    const float2 Ge = make_float2(k0 && f.a_raw.x < S.alpha_max ? f.G.x : 0.0f,
+                                  k1 && f.a_raw.y < S.alpha_max ? f.G.y : 0.0f);
     const float2 sv = __fmul2_rn(dA, Ge);
     sw_mine[(t - glo) ^ zl] = make_float4(sv.x, sv.y, nw.x, nw.y);
   }
