@@ -268,8 +268,10 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restr
 // earlier warps.  The block's keys and values are then laid out digit-major in shared memory and
 // written out by consecutive threads, so each digit's run of the block goes to consecutive
 // addresses (after the scanned histogram's offset for the block).
+// Compiled for 3 resident blocks per SM (80 registers): the kernel waits on memory, and 24 warps hide
+// more of it than the 16 that its unbounded 112 registers allow.
 template <class K>
-__global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(
+__global__ void __launch_bounds__(kRsThreads, 3) radix_scatter_kernel(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, const int64_t* __restrict__ n_dev, int64_t capacity, int shift, int nblocks,
     const uint32_t* __restrict__ offs) {
