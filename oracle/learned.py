@@ -139,6 +139,25 @@ def forward(w: np.ndarray, x: np.ndarray):
     return y, (x0, z1, h1, z2, h2, W1, W2, W3)
 
 
+def bf16_margin(x: np.ndarray) -> np.ndarray:
+    """Distance of float32 values from the nearest bfloat16 rounding boundary (the midpoint between
+    two neighbouring bfloat16 values), as a fraction of the bfloat16 spacing there (0 = on the
+    boundary, 0.5 = on a bfloat16 value)."""
+    a = np.ascontiguousarray(np.asarray(x, np.float32))
+    low = (a.view(np.uint32) & 0xFFFF).astype(np.float64)
+    return np.abs(low - 32768.0) / 65536.0
+
+
+def forward_margins(w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Per point, the smallest bf16_margin of the two hidden activations before their bfloat16
+    rounding: a float32 evaluation that lands within its rounding error of a boundary may round the
+    other way there (the inputs are float32 values, identical on every side)."""
+    _, (x0, z1, h1, z2, h2, W1, W2, W3) = forward(w, x)
+    g1 = gelu(z1)
+    g2 = gelu(z2)
+    return np.minimum(bf16_margin(g1).min(axis=1), bf16_margin(g2).min(axis=1))
+
+
 def _left(p):
     a, b, c, d = p
     return np.array([[a, -d, c, b], [d, a, -b, c], [-c, b, a, d], [-b, -c, -d, a]])

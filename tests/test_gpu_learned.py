@@ -78,10 +78,15 @@ def test_mlp_forward_matches_oracle(dev):
     out = torch.zeros(n, 12, device=dev)
     L.i4d_mlp_forward(_t(x, dev), _t(w, dev), out)
     want, _ = OL.forward(w, x)
-    err = np.abs(out.cpu().numpy() - want)
-    # a hidden activation that lands on a bf16 rounding boundary can round the other way in float32
-    assert np.quantile(err, 0.99) < 1e-4
-    assert err.max() < 5e-3
+    err = np.abs(out.cpu().numpy() - want).max(axis=1)
+    # a hidden activation within float32 rounding (~1e-5 relative, 2e-3 of a bfloat16 spacing) of a
+    # bfloat16 rounding boundary may round the other way: such points may differ by a few bfloat16
+    # steps of one activation times its weights; every other point matches to 1e-4
+    near = OL.forward_margins(w, x) < 2e-3
+    print(f"points with an activation at a bf16 rounding boundary: {int(near.sum())} of {n}")
+    assert near.sum() < 0.5 * n
+    assert err[~near].max() < 1e-4, float(err[~near].max())
+    assert err[near].max() < 5e-3
 
 
 def test_mlp_weight_gradient_matches_oracle(dev):

@@ -117,3 +117,21 @@ def test_knn3_scale_matches_brute_force_window_search():
     got = OL.knn3_scale(xyz, voxel, radius=2, k0=4)      # small first query exercises the widening
     assert np.sum(want == voxel) >= 10                   # the fallback case is covered
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+
+
+def test_bf16_margin_locates_rounding_boundaries():
+    """bf16_margin is 0 exactly where bfloat16 rounding changes value (checked with torch's
+    float32 -> bfloat16 cast on both sides of the boundary) and 0.5 on bfloat16 values."""
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(4)
+    v = r.normal(size=2000).astype(np.float32)
+    b = torch.from_numpy(v).to(torch.bfloat16).float().numpy()
+    assert np.allclose(OL.bf16_margin(b), 0.5)
+    # the midpoint above each bfloat16 value: half a bfloat16 spacing (16 low bits = 0x8000)
+    mid = (b.view(np.uint32) | np.uint32(0x8000)).view(np.float32)
+    assert np.all(OL.bf16_margin(mid) == 0.0)
+    lo = np.nextafter(mid, np.float32(0)).astype(np.float32)
+    hi = np.nextafter(mid, np.float32(np.inf) * np.sign(mid)).astype(np.float32)
+    rl = torch.from_numpy(lo).to(torch.bfloat16).float().numpy()
+    rh = torch.from_numpy(hi).to(torch.bfloat16).float().numpy()
+    assert np.all(rl != rh)
