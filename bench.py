@@ -4,8 +4,8 @@
 Workload: a seeded 200-frame 640x360 depth video of a room with three moving spheres (46.08 M
 back-projected points) is pruned on a 0.01 voxel grid to ~1.13 M 4D Gaussians (heuristic init);
 one step renders a batch of 8 views at distinct frame times (4 x 960x540 + 4 x 480x270) forward
-and backward through the rasterizer, takes an L1 loss against targets rendered from a hidden
-seeded 4D Gaussian scene of the same room, and applies a fused Adam update.
+and backward through the rasterizer, takes the (1 - 0.2) L1 + 0.2 D-SSIM loss against targets
+rendered from a hidden seeded 4D Gaussian scene of the same room, and applies a fused Adam update.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--eager]
 

@@ -15,9 +15,14 @@
  *   - Isotropic variant with R = I and one shared spatial scale (Sec. 3.3, "Isotropic Gaussian").
  *   - EWA projection, per-pixel depth-sorted front-to-back alpha compositing and the analytic
  *     backward: the 3D Gaussian splatting renderer the paper builds on (Sec. 3.1, Eq. 3).
- *   - Back-projection of depth maps (Eq. 5) and voxel-grid pruning: points are assigned to
- *     voxels by division with S_v, aggregated per voxel into a centroid with averaged
- *     attributes, and voxels with too little support are dropped (Sec. 3.2, "Grid Pruning").
+ *   - Back-projection of depth maps (Eq. 5), in float64 and as a fixed sequence of correctly
+ *     rounded float32 operations, and voxel-grid pruning: points are assigned to voxels by
+ *     division with S_v, aggregated per voxel into a centroid with averaged attributes, and
+ *     voxels with too little support are dropped (Sec. 3.2, "Grid Pruning").
+ *   - The tile lists of the binning step: the tiles that hold a pixel centre where a Gaussian can
+ *     be blended, in (depth, id) order.
+ *   - Every valid colour of a pixel whose threshold, T-stop or depth-order decisions sit within a
+ *     margin of going the other way (the results a float32 pipeline may legitimately produce).
  *
  * Readings where the paper is silent (thresholds, pixel-centre convention, tie order, ...)
  * are the constants passed in `settings` and the conventions documented at each function.

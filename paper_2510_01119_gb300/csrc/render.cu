@@ -322,10 +322,10 @@ __global__ void __launch_bounds__(TW * TH / 2, fwd_min_blocks<TW, TH>()) render_
 }
 
 // Backward state of the thread's two pixels (float2 lanes): transmittance in front of the next
-// (nearer) fragment, the negated colour composited behind it, upstream gradient, and the positions
-// of the pixels' last blended fragments.
+// (nearer) fragment, uNS = -sum_c u_c S_c with S_c the colour composited behind it (the only form of
+// S the gradient needs), the upstream gradient u, and the pixels' stop positions.
 struct PairBwd {
-  float2 T, NSr, NSg, NSb, ur, ug, ub;
+  float2 T, uNS, ur, ug, ub;
   uint32_t L0, L1;
 };
 
@@ -506,16 +506,11 @@ __device__ __forceinline__ void phase_a(const SharedStage& stg, const uint8_t* m
     // transmittance in front of this fragment
     const float2 Tk = __ffma2_rn(P.T, __fmul2_rn(ae, iom), P.T);
     const float2 nw = __fmul2_rn(make_float2(-ae.x, -ae.y), Tk);  // -alpha T_k
-    // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = sum_c u_c (T c_k - S_c) / (1 - alpha),
-    // S_c the colour composited behind, T the transmittance behind
-    const float2 cr = f2(b.w), cg = f2(c.x), cb = f2(c.y);
-    const float2 yr = __ffma2_rn(P.T, cr, P.NSr);
-    const float2 yg = __ffma2_rn(P.T, cg, P.NSg);
-    const float2 yb = __ffma2_rn(P.T, cb, P.NSb);
-    const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.ub, yb, __ffma2_rn(P.ug, yg, __fmul2_rn(P.ur, yr))));
-    P.NSr = __ffma2_rn(nw, cr, P.NSr);
-    P.NSg = __ffma2_rn(nw, cg, P.NSg);
-    P.NSb = __ffma2_rn(nw, cb, P.NSb);
+    // dL/dalpha = sum_c u_c (T_k c_k - S_c / (1 - alpha)) = (T (u . c_k) + uNS) / (1 - alpha), T the
+    // transmittance behind; the colour behind grows by alpha T_k c_k, so uNS by -alpha T_k (u . c_k)
+    const float2 uc = __ffma2_rn(P.ub, f2(c.y), __ffma2_rn(P.ug, f2(c.x), __fmul2_rn(P.ur, f2(b.w))));
+    const float2 dA = __fmul2_rn(iom, __ffma2_rn(P.T, uc, P.uNS));
+    P.uNS = __ffma2_rn(nw, uc, P.uNS);
     P.T = Tk;
     // alpha = o_t G carries the gradient only below the alpha_max cap
     const float2 Ge = make_float2(k0 && f.a_raw.x < S.alpha_max ? f.G.x : 0.0f,
@@ -558,7 +553,7 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
   const float2 fy = make_float2((float)wp.py0 + 0.5f, (float)wp.py0 + 1.5f);
   const int64_t HW = (int64_t)tc.W * tc.H;
   PairBwd P;
-  P.T = P.NSr = P.NSg = P.NSb = P.ur = P.ug = P.ub = f2(0.0f);
+  P.T = P.uNS = P.ur = P.ug = P.ub = f2(0.0f);
   P.L0 = P.L1 = 0u;
   if (in0) {
     const int64_t p = vt.pix_off[tc.v] + (int64_t)wp.py0 * tc.W + wp.px;
@@ -581,9 +576,8 @@ __global__ void __launch_bounds__(TW * TH / 2, bwd_min_blocks<TW, TH>()) render_
   const int zl = pair_swz(l16);
   W.urg[wp.half][(l16 & 8) | zl] = make_float4(P.ur.x, P.ur.y, P.ug.x, P.ug.y);
   W.ub[wp.half][l16] = P.ub;
-  P.NSr = __fmul2_rn(P.T, f2(-S.bg[0]));
-  P.NSg = __fmul2_rn(P.T, f2(-S.bg[1]));
-  P.NSb = __fmul2_rn(P.T, f2(-S.bg[2]));
+  // behind the last fragment: the background, weighted by T_final
+  P.uNS = __fmul2_rn(P.T, __ffma2_rn(P.ub, f2(-S.bg[2]), __ffma2_rn(P.ug, f2(-S.bg[1]), __fmul2_rn(P.ur, f2(-S.bg[0])))));
   // this warp never needs entries at or past its pixels' stop positions, and below the smallest stop
   // position of its pixels in the view every kept fragment was blended (pixels outside the view have
   // T = 0 and no upstream gradient: whatever they take contributes exactly zero)
