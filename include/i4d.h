@@ -176,8 +176,10 @@ I4D_API int32_t i4d_slice_project(const i4d_gaussians* g, const i4d_views* views
  *   capacity       size of ids (and of the key arrays in the workspace)
  *   ids            DEVICE out, capacity uint32: Gaussian id of each sorted pair
  *   ranges         DEVICE out, 3 * total_tiles uint32: [start, end) per tile (all views), then the
- *                  tile indices ordered by decreasing list length (the order in which the
- *                  compositing kernels take tiles, so that the longest ones start first)
+ *                  tile indices ordered by decreasing octave of list length, floor(log2(length +
+ *                  1)), and by tile index within an octave (the order in which the compositing
+ *                  kernels take tiles: the longest start first, and neighbouring tiles run
+ *                  together so that they share the records they read in L2)
  *   n_inst         DEVICE out, 1 int64: number of pairs (may exceed capacity)
  *   status         DEVICE out, 1 int32: I4D_OK, or I4D_ERR_CAPACITY when n_inst > capacity
  *                  (the sorted output is then invalid; retry with capacity >= n_inst)

@@ -20,6 +20,10 @@ normal CDF.  y = (log s_t, v_x, v_y, v_z, q_l (4), q_r (4)).
 
 loss (mean over points): w_st (y0 - log s_t*)^2 + w_v |v - v*|^2 + w_R ||R(q_l, q_r) - R*||_F^2 with
 R(q_l, q_r) the 4D rotation v -> q_l v q_r of the normalised quaternions (sign-free target).
+
+Backward: bfloat16 operands with float32 accumulation, like the forward: the gradient entering
+each layer's matrix product is rounded to bfloat16 before the two products that use it (see
+backward()); the exact straight-through gradient is kept beside it for the pins.
 """
 from __future__ import annotations
 
@@ -208,19 +212,31 @@ def loss_and_grad(y: np.ndarray, target: np.ndarray, w_st=1.0, w_v=1.0, w_R=1.0)
     return loss / n, dy / n
 
 
-def backward(w: np.ndarray, cache, dy: np.ndarray) -> np.ndarray:
+def backward(w: np.ndarray, cache, dy: np.ndarray, operands: str = "bf16") -> np.ndarray:
     """Gradient of sum(dy * y) with respect to the float32 master weights (straight through the
-    bfloat16 rounding of the weights and activations), in the packed weight layout."""
+    bfloat16 rounding of the weights and activations), in the packed weight layout.
+
+    operands="bf16" (the training kernels' arithmetic: bfloat16 operands, float32 accumulation):
+    the gradient flowing into each layer's matrix product, dL/d(W h) (dy for the output layer,
+    dz2 and dz1 for the hidden ones), is rounded to bfloat16 before it multiplies the bfloat16
+    activations (weight gradients) and the bfloat16 weights (gradient of the layer below); the
+    bias gradients sum the unrounded values.  operands="exact": no rounding in the backward, the
+    exact gradient of the forward with straight-through rounding."""
+    if operands not in ("bf16", "exact"):
+        raise ValueError(operands)
+    r = bf16 if operands == "bf16" else (lambda a: np.asarray(a, np.float64))
     x0, z1, h1, z2, h2, W1, W2, W3 = cache
-    dW3 = dy.T @ h2
+    dyr = r(dy)
+    dW3 = dyr.T @ h2
     db3 = dy.sum(0)
-    dh2 = dy @ W3
+    dh2 = dyr @ W3
     dz2 = dh2 * gelu_grad(z2)
-    dW2 = dz2.T @ h1
+    dz2r = r(dz2)
+    dW2 = dz2r.T @ h1
     db2 = dz2.sum(0)
-    dh1 = dz2 @ W2
+    dh1 = dz2r @ W2
     dz1 = dh1 * gelu_grad(z1)
-    dW1 = dz1.T @ x0
+    dW1 = r(dz1).T @ x0
     db1 = dz1.sum(0)
     return np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
 

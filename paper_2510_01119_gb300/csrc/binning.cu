@@ -388,35 +388,61 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __rest
   }
 }
 
-// Tiles ordered by decreasing list length, in buckets of a quarter octave (order inside a bucket is
-// arbitrary: it only changes which CTA starts first, never a result).  One CTA of 1024 threads.
-constexpr int kOrderBuckets = 80;
+// Tiles ordered longest first by octave of list length; inside an octave the tiles keep their index
+// order (view by view, row-major), so that the CTAs in flight at one time work on neighbouring tiles
+// and share the records they gather in L2 (on the 1.13M-Gaussian, 8-view training batch the
+// backward's DRAM traffic falls from 2.26 to 1.80 GB against quarter-octave buckets, for 0.6% more
+// time in the two compositing kernels).  The order only decides which CTA starts first, never a
+// result.  One CTA of 1024 threads: a stable counting sort, ranked per warp with match_any and per
+// bucket by a scan over the warps.
+constexpr int kOrderBuckets = 33;  // octaves of lengths below 2^33
 
-__device__ __forceinline__ int length_bucket(uint32_t len) {
-  const int b = (int)floorf(4.0f * log2f((float)len + 1.0f));
-  return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+  return kOrderBuckets - 1 - min((int)floorf(log2f((float)len + 1.0f)), kOrderBuckets - 1);
 }
 
 __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __restrict__ ranges, int T,
                                                           uint32_t* __restrict__ order) {
-  __shared__ uint32_t hist[kOrderBuckets];
-  for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) hist[k] = 0;
+  __shared__ uint32_t base[kOrderBuckets];
+  __shared__ uint32_t warp_pos[32][kOrderBuckets];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* wp = &warp_pos[0][0];
+  for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) base[k] = 0;
+  for (int k = threadIdx.x; k < 32 * kOrderBuckets; k += blockDim.x) wp[k] = 0;
   __syncthreads();
-  for (int t = threadIdx.x; t < T; t += blockDim.x)
-    atomicAdd(&hist[length_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+  for (int t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&base[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
     for (int k = 0; k < kOrderBuckets; ++k) {
-      const uint32_t c = hist[k];
-      hist[k] = run;
+      const uint32_t c = base[k];
+      base[k] = run;
       run += c;
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < T; t += blockDim.x) {
-    const uint32_t pos = atomicAdd(&hist[length_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
-    order[pos] = (uint32_t)t;
+  for (int t0 = 0; t0 < T; t0 += blockDim.x) {
+    const int t = t0 + (int)threadIdx.x;
+    const int b = t < T ? order_bucket(ranges[2 * t + 1] - ranges[2 * t]) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (b >= 0 && rank == 0) warp_pos[warp][b] = __popc(peers);
+    __syncthreads();
+    // per bucket: warp counts -> positions (warps in index order), bucket base advanced by the chunk
+    for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) {
+      uint32_t run = base[k];
+      for (int w = 0; w < 32; ++w) {
+        const uint32_t c = warp_pos[w][k];
+        warp_pos[w][k] = run;
+        run += c;
+      }
+      base[k] = run;
+    }
+    __syncthreads();
+    if (b >= 0) order[warp_pos[warp][b] + rank] = (uint32_t)t;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 32 * kOrderBuckets; k += blockDim.x) wp[k] = 0;
+    __syncthreads();
   }
 }
 

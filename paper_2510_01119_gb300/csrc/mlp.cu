@@ -4,10 +4,12 @@
 // Forward (inference and training): one warp per 16 points; the three layers run on the tensor
 // cores with mma.sync m16n8k16 (bf16 x bf16 -> f32); the accumulators of one layer, biased and
 // passed through GELU, are rounded to bf16 and become the next layer's A fragments in registers.
-// Training: the same forward per 64-point chunk into shared memory, the loss and its gradient per
-// point (log s_t and velocity squared errors, rotation compared as the 16 entries of R(q_l, q_r)),
-// the backward through the bf16-rounded weights and activations in float32, and per-block partial
-// weight gradients accumulated in registers, summed afterwards by a reduction kernel.
+// Training: the same forward per 64-point chunk, the loss and its gradient per point (log s_t and
+// velocity squared errors, rotation compared as the 16 entries of R(q_l, q_r)), and the backward on
+// the tensor cores too: bfloat16 operands (the gradient entering each product rounded once, the
+// weights and activations as the forward used them), float32 accumulation; per-block partial
+// weight gradients held in the mma accumulators across chunks, summed afterwards by a reduction
+// kernel.
 #include <cuda_bf16.h>
 
 #include "gauss_math.cuh"
@@ -92,9 +94,9 @@ struct WarpForward {
   uint32_t a2[4][4], a3[4][4];
 };
 
+// A fragments of the input rows (k-blocks of 16 features) for a warp's 16 rows
 template <class XLoad>
-__device__ __forceinline__ void warp_forward(const MlpSmem& s, XLoad xl, WarpForward& F, int g, int t) {
-  uint32_t a1[4][4];
+__device__ __forceinline__ void input_fragments(XLoad xl, uint32_t (*a1)[4], int g, int t) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     a1[k][0] = pack_bf16(xl(g, 16 * k + 2 * t), xl(g, 16 * k + 2 * t + 1));
@@ -102,10 +104,10 @@ __device__ __forceinline__ void warp_forward(const MlpSmem& s, XLoad xl, WarpFor
     a1[k][2] = pack_bf16(xl(g, 16 * k + 8 + 2 * t), xl(g, 16 * k + 9 + 2 * t));
     a1[k][3] = pack_bf16(xl(g + 8, 16 * k + 8 + 2 * t), xl(g + 8, 16 * k + 9 + 2 * t));
   }
-  // the A-fragment register order is (row g | row g+8 | row g, +8 cols | row g+8, +8 cols); the
-  // hidden layers write (lo, hi) of n-tile 2s into slots 0, 1 and of n-tile 2s+1 into 2, 3
-  hidden_layer(s.w1, s.b1, a1, F.z1, F.a2, g, t);
-  hidden_layer(s.w2, s.b2, F.a2, F.z2, F.a3, g, t);
+}
+
+// Output layer: y (2 n-tiles of C fragments) = bf16(h2) W3^T + b3
+__device__ __forceinline__ void output_layer(const MlpSmem& s, const uint32_t (*a3)[4], float (*y)[4], int g, int t) {
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -113,14 +115,25 @@ __device__ __forceinline__ void warp_forward(const MlpSmem& s, XLoad xl, WarpFor
     for (int k = 0; k < 4; ++k) {
       const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&s.w3[8 * j + g][16 * k + 2 * t]);
       const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&s.w3[8 * j + g][16 * k + 8 + 2 * t]);
-      mma16816(c, F.a3[k], b0, b1);
+      mma16816(c, a3[k], b0, b1);
     }
     const float bb0 = s.b3[8 * j + 2 * t], bb1 = s.b3[8 * j + 2 * t + 1];
-    F.y[j][0] = c[0] + bb0;
-    F.y[j][1] = c[1] + bb1;
-    F.y[j][2] = c[2] + bb0;
-    F.y[j][3] = c[3] + bb1;
+    y[j][0] = c[0] + bb0;
+    y[j][1] = c[1] + bb1;
+    y[j][2] = c[2] + bb0;
+    y[j][3] = c[3] + bb1;
   }
+}
+
+template <class XLoad>
+__device__ __forceinline__ void warp_forward(const MlpSmem& s, XLoad xl, WarpForward& F, int g, int t) {
+  uint32_t a1[4][4];
+  input_fragments(xl, a1, g, t);
+  // the A-fragment register order is (row g | row g+8 | row g, +8 cols | row g+8, +8 cols); the
+  // hidden layers write (lo, hi) of n-tile 2s into slots 0, 1 and of n-tile 2s+1 into 2, 3
+  hidden_layer(s.w1, s.b1, a1, F.z1, F.a2, g, t);
+  hidden_layer(s.w2, s.b2, F.a2, F.z2, F.a3, g, t);
+  output_layer(s, F.a3, F.y, g, t);
 }
 
 __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ feat, int64_t n,
@@ -155,14 +168,30 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
 }
 
 // ---- training ------------------------------------------------------------------------------------------
+// Per block, chunks of 64 points; warp w owns points [16 w, 16 w + 16) of the chunk in the forward and
+// in the gradient of the pre-activations, and rows [16 w, 16 w + 16) of dW1 and dW2 (and columns
+// [16 w, 16 w + 16) of dW3) in the weight gradient, whose m16n8k16 accumulators it keeps across
+// chunks.  Every product takes bfloat16 operands: the gradient entering a layer's product
+// (dL/dy, dz2, dz1) is rounded to bfloat16 once and used for both that layer's weight gradient and
+// the gradient of the layer below; the bias gradients sum the float32 values.  Operands of the
+// weight-gradient products (K = the chunk's points) are stored transposed, [feature][point], with a
+// padded row so that the fragment loads are free of bank conflicts.
+constexpr int kTS = 72;  // row stride (bf16) of the transposed tiles
+constexpr int kW3S = 24;  // row stride of the transposed W3 (16 outputs + pad)
+
 struct TrainSmem {
-  MlpSmem w;
-  float x0[64][kIn];   // bf16-rounded inputs
-  float z1[64][kH];    // pre-activations, overwritten by their gradients
-  float h1[64][kH];    // bf16-rounded activations
-  float z2[64][kH];
-  float h2[64][kH];
-  float y[64][kOutPad];  // outputs, overwritten by their gradients
+  MlpSmem w;                           // forward operands
+  __nv_bfloat16 w2t[kH][kTS];          // w2t[i][o] = W2[o][i]
+  __nv_bfloat16 w3t[kH][kW3S];         // w3t[i][o] = W3[o][i], outputs 12..15 zero
+  __nv_bfloat16 x0t[kIn][kTS];         // bf16 inputs, [feature][point]
+  __nv_bfloat16 h1t[kH][kTS];          // bf16 activations, [unit][point]
+  __nv_bfloat16 h2t[kH][kTS];
+  __nv_bfloat16 d1t[kH][kTS];          // bf16(dz1), [unit][point]
+  __nv_bfloat16 d2t[kH][kTS];          // bf16(dz2)
+  __nv_bfloat16 dyt[kOutPad][kTS];     // bf16(dL/dy), [output][point], outputs 12..15 zero
+  float2 z1[64][kH / 2];               // first-layer pre-activations (float32), C-fragment pairs
+  float y[64][kOutPad];                // outputs, overwritten by dL/dy (float32)
+  float bsum[4][2 * kH];               // per warp: column sums of dz1 | dz2 over its 16 points
 };
 
 // Loss of one point and its gradient with respect to the 12 outputs (scaled by inv_n).
@@ -227,6 +256,58 @@ __device__ float point_loss(const float* y, const float* tg, float w_st, float w
   return loss;
 }
 
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// A fragments of a warp's 16 rows (bf16 pairs along the row) -> transposed tile dst[col][row]
+__device__ __forceinline__ void store_a_transposed(__nv_bfloat16 (*dst)[kTS], const uint32_t (*a)[4], int r0, int g,
+                                                   int t) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int slot = 0; slot < 4; ++slot) {
+      const int col = 16 * s + 8 * (slot >> 1) + 2 * t, row = r0 + g + 8 * (slot & 1);
+      const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&a[s][slot]);
+      dst[col][row] = v.x;
+      dst[col + 1][row] = v.y;
+    }
+}
+
+// Column sums of a C fragment over the warp's 16 rows (lanes of equal t hold the same columns)
+__device__ __forceinline__ float2 column_sums(float d0, float d1, float d2, float d3) {
+  float s0 = d0 + d2, s1 = d1 + d3;
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  return make_float2(s0, s1);
+}
+
+// d = c * gelu'(z) for n-tile j of a layer: column sums into bsum, bf16(d) into the transposed tile
+// and into the A fragments a (k-block j / 2) of the next product
+__device__ __forceinline__ void pre_activation_grad(const float* c, const float* z, int j, int r0, int g, int t,
+                                                    float* bsum, __nv_bfloat16 (*dt)[kTS], uint32_t (*a)[4]) {
+  const float d0 = c[0] * gelu_grad(z[0]), d1 = c[1] * gelu_grad(z[1]);
+  const float d2 = c[2] * gelu_grad(z[2]), d3 = c[3] * gelu_grad(z[3]);
+  const float2 cs = column_sums(d0, d1, d2, d3);
+  const int col = 8 * j + 2 * t;
+  if (g == 0) {
+    bsum[col] = cs.x;
+    bsum[col + 1] = cs.y;
+  }
+  const uint32_t lo = pack_bf16(d0, d1), hi = pack_bf16(d2, d3);
+  if (a) {
+    a[j >> 1][(j & 1) * 2 + 0] = lo;
+    a[j >> 1][(j & 1) * 2 + 1] = hi;
+  }
+  const __nv_bfloat162 vl = *reinterpret_cast<const __nv_bfloat162*>(&lo);
+  const __nv_bfloat162 vh = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+  dt[col][r0 + g] = vl.x;
+  dt[col + 1][r0 + g] = vl.y;
+  dt[col][r0 + g + 8] = vh.x;
+  dt[col + 1][r0 + g + 8] = vh.y;
+}
+
 __global__ void __launch_bounds__(128) mlp_grad_kernel(const float* __restrict__ feat, const float* __restrict__ tgt,
                                                        int64_t n, const float* __restrict__ w, float w_st, float w_v,
                                                        float w_R, float* __restrict__ partial,
@@ -235,58 +316,61 @@ __global__ void __launch_bounds__(128) mlp_grad_kernel(const float* __restrict__
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   __shared__ float red[4];
   load_weights(S.w, w);
+  for (int k = threadIdx.x; k < kH * kH; k += blockDim.x) S.w2t[k % kH][k / kH] = __float2bfloat16_rn(w[kOffW2 + k]);
+  for (int k = threadIdx.x; k < kOutPad * kH; k += blockDim.x) {
+    const int o = k / kH, i = k % kH;
+    S.w3t[i][o] = __float2bfloat16_rn(o < kOut ? w[kOffW3 + o * kH + i] : 0.0f);
+  }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = warp * 16;
   const float inv_n = 1.0f / (float)n;
-  // owned weight-gradient entries: W1 and W2 row o1 = tid / 2, columns [32 (tid % 2), +32);
-  // W3 entries 6 tid .. 6 tid + 5; biases: b1 (tid < 64), b2 (tid >= 64), b3 (tid < 12)
-  const int o1 = tid >> 1, c1 = (tid & 1) * 32;
-  float a1[32], a2[32], a3[6], ab = 0.0f, ab3 = 0.0f;
+  float gW1[8][4], gW2[8][4], gW3[2][4];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) a1[k] = a2[k] = 0.0f;
+  for (int j = 0; j < 8; ++j)
 #pragma unroll
-  for (int k = 0; k < 6; ++k) a3[k] = 0.0f;
-  float loss = 0.0f;
+    for (int e = 0; e < 4; ++e) gW1[j][e] = gW2[j][e] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gW3[j][e] = 0.0f;
+  float gb = 0.0f, gb3 = 0.0f, loss = 0.0f;
   for (int64_t base = (int64_t)blockIdx.x * 64; base < n; base += (int64_t)gridDim.x * 64) {
     __syncthreads();
     for (int k = tid; k < 64 * kIn; k += 128) {
       const int64_t p = base + k / kIn;
-      const float v = p < n ? feat[p * kIn + (k % kIn)] : 0.0f;
-      (&S.x0[0][0])[k] = __bfloat162float(__float2bfloat16_rn(v));
+      S.x0t[k % kIn][k / kIn] = __float2bfloat16_rn(p < n ? feat[p * kIn + (k % kIn)] : 0.0f);
     }
     __syncthreads();
+    // forward of the warp's 16 points; z1 goes to shared memory, z2 stays in registers
+    float z2[8][4];
     {
-      const int r0 = warp * 16;
-      auto xl = [&](int r, int c) -> float { return S.x0[r0 + r][c]; };
-      WarpForward F;
-      warp_forward(S.w, xl, F, g, t);
+      uint32_t a1[4][4], a2[4][4], a3[4][4];
+      input_fragments([&](int r, int c) -> float { return __bfloat162float(S.x0t[c][r0 + r]); }, a1, g, t);
+      {
+        float z1[8][4];
+        hidden_layer(S.w.w1, S.w.b1, a1, z1, a2, g, t);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int col = 8 * j + 2 * t;
-        S.z1[r0 + g][col] = F.z1[j][0];
-        S.z1[r0 + g][col + 1] = F.z1[j][1];
-        S.z1[r0 + g + 8][col] = F.z1[j][2];
-        S.z1[r0 + g + 8][col + 1] = F.z1[j][3];
-        S.z2[r0 + g][col] = F.z2[j][0];
-        S.z2[r0 + g][col + 1] = F.z2[j][1];
-        S.z2[r0 + g + 8][col] = F.z2[j][2];
-        S.z2[r0 + g + 8][col + 1] = F.z2[j][3];
+        for (int j = 0; j < 8; ++j) {  // read back by the same lanes in the gradient of z1
+          S.z1[r0 + g][4 * j + t] = make_float2(z1[j][0], z1[j][1]);
+          S.z1[r0 + g + 8][4 * j + t] = make_float2(z1[j][2], z1[j][3]);
+        }
       }
+      store_a_transposed(S.h1t, a2, r0, g, t);
+      hidden_layer(S.w.w2, S.w.b2, a2, z2, a3, g, t);
+      store_a_transposed(S.h2t, a3, r0, g, t);
+      float y[2][4];
+      output_layer(S.w, a3, y, g, t);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int col = 8 * j + 2 * t;
-        S.y[r0 + g][col] = F.y[j][0];
-        S.y[r0 + g][col + 1] = F.y[j][1];
-        S.y[r0 + g + 8][col] = F.y[j][2];
-        S.y[r0 + g + 8][col + 1] = F.y[j][3];
+        S.y[r0 + g][col] = y[j][0];
+        S.y[r0 + g][col + 1] = y[j][1];
+        S.y[r0 + g + 8][col] = y[j][2];
+        S.y[r0 + g + 8][col + 1] = y[j][3];
       }
     }
     __syncthreads();
-    // activations (bf16-rounded, as the forward used them)
-    for (int k = tid; k < 64 * kH; k += 128) {
-      (&S.h1[0][0])[k] = __bfloat162float(__float2bfloat16_rn(gelu((&S.z1[0][0])[k])));
-      (&S.h2[0][0])[k] = __bfloat162float(__float2bfloat16_rn(gelu((&S.z2[0][0])[k])));
-    }
-    // loss and dL/dy per point
+    // loss and dL/dy per point (float32, and its bf16 rounding transposed)
     if (tid < 64) {
       const int64_t p = base + tid;
       float dy[kOut];
@@ -297,57 +381,98 @@ __global__ void __launch_bounds__(128) mlp_grad_kernel(const float* __restrict__
         for (int k = 0; k < kOut; ++k) dy[k] = 0.0f;
       }
 #pragma unroll
-      for (int k = 0; k < kOut; ++k) S.y[tid][k] = dy[k];
+      for (int k = 0; k < kOutPad; ++k) {
+        const float v = k < kOut ? dy[k] : 0.0f;
+        S.y[tid][k] = v;
+        S.dyt[k][tid] = __float2bfloat16_rn(v);
+      }
     }
     __syncthreads();
-    // dz2 = (dy W3) * gelu'(z2)
-    for (int k = tid; k < 64 * kH; k += 128) {
-      const int p = k / kH, h = k % kH;
-      float acc = 0.0f;
+    {
+      // dz2 = (bf16(dy) W3) * gelu'(z2) for the warp's 16 points (K = 16 outputs)
+      uint32_t ady[4];
+      ady[0] = pack_bf16(S.y[r0 + g][2 * t], S.y[r0 + g][2 * t + 1]);
+      ady[1] = pack_bf16(S.y[r0 + g + 8][2 * t], S.y[r0 + g + 8][2 * t + 1]);
+      ady[2] = pack_bf16(S.y[r0 + g][2 * t + 8], S.y[r0 + g][2 * t + 9]);
+      ady[3] = pack_bf16(S.y[r0 + g + 8][2 * t + 8], S.y[r0 + g + 8][2 * t + 9]);
+      uint32_t ad2[4][4];
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) acc += S.y[p][o] * __bfloat162float(S.w.w3[o][h]);
-      S.z2[p][h] = acc * gelu_grad(S.z2[p][h]);
-    }
-    __syncthreads();
-    // dz1 = (dz2 W2) * gelu'(z1)
-    for (int k = tid; k < 64 * kH; k += 128) {
-      const int p = k / kH, h = k % kH;
-      float acc = 0.0f;
-#pragma unroll 8
-      for (int o = 0; o < kH; ++o) acc += S.z2[p][o] * __bfloat162float(S.w.w2[o][h]);
-      S.z1[p][h] = acc * gelu_grad(S.z1[p][h]);
-    }
-    __syncthreads();
-    // weight-gradient partials
-    for (int p = 0; p < 64; ++p) {
-      const float d1 = S.z1[p][o1], d2 = S.z2[p][o1];
+      for (int j = 0; j < 8; ++j) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        mma16816(c, ady, ld_pair(&S.w3t[8 * j + g][2 * t]), ld_pair(&S.w3t[8 * j + g][2 * t + 8]));
+        pre_activation_grad(c, z2[j], j, r0, g, t, &S.bsum[warp][kH], S.d2t, ad2);
+      }
+      // dz1 = (bf16(dz2) W2) * gelu'(z1) (K = 64 units)
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        a1[k] += d1 * S.x0[p][c1 + k];
-        a2[k] += d2 * S.h1[p][c1 + k];
+      for (int j = 0; j < 8; ++j) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          mma16816(c, ad2[s], ld_pair(&S.w2t[8 * j + g][16 * s + 2 * t]),
+                   ld_pair(&S.w2t[8 * j + g][16 * s + 8 + 2 * t]));
+        const float2 za = S.z1[r0 + g][4 * j + t], zb = S.z1[r0 + g + 8][4 * j + t];
+        const float z[4] = {za.x, za.y, zb.x, zb.y};
+        pre_activation_grad(c, z, j, r0, g, t, &S.bsum[warp][0], S.d1t, nullptr);
+      }
+    }
+    __syncthreads();
+    // weight gradients over the chunk's 64 points (K): dW1 += bf16(dz1)^T x0, dW2 += bf16(dz2)^T h1,
+    // dW3 += bf16(dy)^T h2
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int k0 = 16 * s + 2 * t;
+      uint32_t a1[4] = {ld_pair(&S.d1t[r0 + g][k0]), ld_pair(&S.d1t[r0 + g + 8][k0]), ld_pair(&S.d1t[r0 + g][k0 + 8]),
+                        ld_pair(&S.d1t[r0 + g + 8][k0 + 8])};
+      uint32_t a2[4] = {ld_pair(&S.d2t[r0 + g][k0]), ld_pair(&S.d2t[r0 + g + 8][k0]), ld_pair(&S.d2t[r0 + g][k0 + 8]),
+                        ld_pair(&S.d2t[r0 + g + 8][k0 + 8])};
+      uint32_t a3[4] = {ld_pair(&S.dyt[g][k0]), ld_pair(&S.dyt[g + 8][k0]), ld_pair(&S.dyt[g][k0 + 8]),
+                        ld_pair(&S.dyt[g + 8][k0 + 8])};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        mma16816(gW1[j], a1, ld_pair(&S.x0t[8 * j + g][k0]), ld_pair(&S.x0t[8 * j + g][k0 + 8]));
+        mma16816(gW2[j], a2, ld_pair(&S.h1t[8 * j + g][k0]), ld_pair(&S.h1t[8 * j + g][k0 + 8]));
       }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int e = 6 * tid + k;
-        a3[k] += S.y[p][e / kH] * S.h2[p][e % kH];
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = 2 * warp + jj;
+        mma16816(gW3[jj], a3, ld_pair(&S.h2t[8 * j + g][k0]), ld_pair(&S.h2t[8 * j + g][k0 + 8]));
       }
-      ab += tid < 64 ? S.z1[p][tid] : S.z2[p][tid - 64];
-      if (tid < kOut) ab3 += S.y[p][tid];
     }
+    // bias gradients: float32 sums (thread tid < 64: b1 unit tid; else b2 unit tid - 64; tid < 12: b3)
+    gb += S.bsum[0][tid] + S.bsum[1][tid] + S.bsum[2][tid] + S.bsum[3][tid];
+    if (tid < kOut)
+      for (int p = 0; p < 64; ++p) gb3 += S.y[p][tid];
   }
   float* P = partial + (int64_t)blockIdx.x * kWeights;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    P[kOffW1 + o1 * kIn + c1 + k] = a1[k];
-    P[kOffW2 + o1 * kH + c1 + k] = a2[k];
+  for (int j = 0; j < 8; ++j) {
+    const int o = r0 + g, i = 8 * j + 2 * t;
+    P[kOffW1 + o * kIn + i] = gW1[j][0];
+    P[kOffW1 + o * kIn + i + 1] = gW1[j][1];
+    P[kOffW1 + (o + 8) * kIn + i] = gW1[j][2];
+    P[kOffW1 + (o + 8) * kIn + i + 1] = gW1[j][3];
+    P[kOffW2 + o * kH + i] = gW2[j][0];
+    P[kOffW2 + o * kH + i + 1] = gW2[j][1];
+    P[kOffW2 + (o + 8) * kH + i] = gW2[j][2];
+    P[kOffW2 + (o + 8) * kH + i + 1] = gW2[j][3];
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) P[kOffW3 + 6 * tid + k] = a3[k];
+  for (int jj = 0; jj < 2; ++jj) {
+    const int h = 8 * (2 * warp + jj) + 2 * t;
+    if (g < kOut) {
+      P[kOffW3 + g * kH + h] = gW3[jj][0];
+      P[kOffW3 + g * kH + h + 1] = gW3[jj][1];
+    }
+    if (g + 8 < kOut) {
+      P[kOffW3 + (g + 8) * kH + h] = gW3[jj][2];
+      P[kOffW3 + (g + 8) * kH + h + 1] = gW3[jj][3];
+    }
+  }
   if (tid < 64)
-    P[kOffB1 + tid] = ab;
+    P[kOffB1 + tid] = gb;
   else
-    P[kOffB2 + tid - 64] = ab;
-  if (tid < kOut) P[kOffB3 + tid] = ab3;
+    P[kOffB2 + tid - 64] = gb;
+  if (tid < kOut) P[kOffB3 + tid] = gb3;
   // block loss
   float l = loss;
 #pragma unroll

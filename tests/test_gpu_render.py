@@ -116,6 +116,30 @@ def test_tile_lists_match_oracle(dev, orc, tile):
     assert rep["gpu"] <= 1.5 * rep["needed"]
 
 
+def test_tile_order_is_longest_first_and_stable(dev):
+    """The order in which the compositing kernels take tiles: a permutation of all tiles, by
+    decreasing octave of list length (floor(log2(length + 1))), tile index order inside an octave
+    (over more than one 1024-tile chunk of the ordering kernel)."""
+    g = synth.gaussians_uniform(0)
+    cams = [synth.camera(320, 240, 60.0, time=0.5), synth.camera(75, 41, 55.0, time=0.3)]
+    rast, _, _ = _gpu_render(g, cams, tile=(8, 8))
+    T = rast.total_tiles
+    assert T > 1024
+    rg = rast.ranges[:3 * T].cpu().numpy().astype(np.int64)
+    length, order = rg[1:2 * T:2] - rg[0:2 * T:2], rg[2 * T:]
+    assert np.array_equal(np.sort(order), np.arange(T))
+    f = np.log2(length[order] + 1.0)
+    b = np.floor(f)
+    near = np.abs(f - np.round(f)) < 1e-4           # float32 log2 may put these in either bucket
+    loose = near[:-1] | near[1:]
+    d = np.diff(b)
+    assert np.all((d <= 0) | loose)
+    assert np.all(np.diff(order)[(d == 0) & ~loose] > 0)
+    assert len(np.unique(b)) > 3
+    # every tile with a non-empty list comes before every empty one
+    assert np.all(np.diff((length[order] == 0).astype(int)) >= 0)
+
+
 @pytest.mark.parametrize("mode,deg", [(0, 0), (1, 0), (2, 0), (0, 3)])
 def test_render_forward_matches_oracle(dev, orc, mode, deg):
     g = synth.gaussians_uniform(0, sh_deg=deg, mode=mode)

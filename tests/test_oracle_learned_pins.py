@@ -32,7 +32,7 @@ def test_mlp_forward_backward_match_torch_autograd():
     x = r.normal(size=(40, 64)).astype(np.float32)
     y, cache = OL.forward(w, x)
     dy = r.normal(size=y.shape)
-    g = OL.backward(w, cache, dy)
+    g = OL.backward(w, cache, dy, operands="exact")
 
     def st(t):  # straight-through bfloat16 rounding
         return t + (t.to(torch.float32).to(torch.bfloat16).to(torch.float64) - t).detach()
@@ -52,6 +52,61 @@ def test_mlp_forward_backward_match_torch_autograd():
     assert np.allclose(h.detach().numpy(), y, rtol=1e-12, atol=1e-12)
     (h * torch.from_numpy(dy)).sum().backward()
     assert np.allclose(wt.grad.numpy(), g, rtol=1e-10, atol=1e-12)
+
+
+class _RoundGrad(torch.autograd.Function):
+    """Identity forward; the backward rounds the incoming gradient to bfloat16."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def _torch_mlp_grad(w, x, dy, round_grads):
+    def st(t):  # straight-through bfloat16 rounding of the forward operands
+        return t + (t.to(torch.float32).to(torch.bfloat16).to(torch.float64) - t).detach()
+
+    wt = torch.from_numpy(w.astype(np.float64)).requires_grad_(True)
+    off, layers = 0, []
+    for o, i in OL.LAYER_SHAPES:
+        W = wt[off:off + o * i].view(o, i)
+        off += o * i
+        b = wt[off:off + o]
+        off += o
+        layers.append((st(W), b))
+    h = st(torch.from_numpy(x.astype(np.float64)))
+    for k, (W, b) in enumerate(layers):
+        m = h @ W.T
+        z = (_RoundGrad.apply(m) if round_grads else m) + b
+        h = st(torch.nn.functional.gelu(z)) if k < 2 else z
+    (h * torch.from_numpy(dy)).sum().backward()
+    return wt.grad.numpy()
+
+
+def test_mlp_bf16_operand_backward_matches_torch_autograd():
+    """The training kernels' reading: the gradient entering each matrix product is rounded to
+    bfloat16 (biases take the unrounded sums).  Autograd places that rounding between each product
+    and its bias add; the oracle's backward must agree to float64 rounding, and differ from the
+    exact gradient by about the bfloat16 precision."""
+    r = np.random.default_rng(11)
+    w = (OL.init_weights(5).astype(np.float64) + r.normal(0, 0.05, OL.weight_count())).astype(np.float32)
+    x = r.normal(size=(50, 64)).astype(np.float32)
+    y, cache = OL.forward(w, x)
+    dy = r.normal(size=y.shape) * 1e-3
+    g = OL.backward(w, cache, dy)
+    want = _torch_mlp_grad(w, x, dy, round_grads=True)
+    assert np.allclose(g, want, rtol=1e-10, atol=1e-15)
+    exact = OL.backward(w, cache, dy, operands="exact")
+    assert np.allclose(exact, _torch_mlp_grad(w, x, dy, round_grads=False), rtol=1e-10, atol=1e-15)
+    d = np.linalg.norm(g - exact) / np.linalg.norm(exact)
+    assert 1e-5 < d < 1e-2, d
+    # the biases sum unrounded values: the output-layer bias gradient is the same in both
+    nb3 = OL.LAYER_SHAPES[2][0]
+    assert np.array_equal(g[-nb3:], exact[-nb3:])
 
 
 def test_rotation_loss_gradient_matches_central_differences():
