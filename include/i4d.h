@@ -69,7 +69,8 @@ extern "C" {
 
 #define I4D_MAX_VIEWS 64
 #define I4D_PROJ_FLOATS 16     /* floats per projected record (one 64-byte record) */
-#define I4D_GRAD2D_FLOATS 12   /* floats per (view, Gaussian) 2D-gradient record (3 float4 planes) */
+#define I4D_GRAD2D_FLOATS 9    /* floats per (view, Gaussian) 2D-gradient record: two float4 planes and one
+                                  float plane, each n_views * n long */
 
 enum { I4D_MODE_FULL = 0, I4D_MODE_ISO_ROT = 1, I4D_MODE_ISO_IDENTITY = 2 };
 enum { I4D_LOSS_L1 = 0, I4D_LOSS_MSE = 1 };
@@ -229,7 +230,7 @@ I4D_API int32_t i4d_render_bwd(const i4d_gaussians* g, const i4d_views* views, c
  * run the backward (a C/C++ host whose device heap belongs to its own memory manager, or a real-time
  * loop that must not stall on cudaMalloc).  The paper has no counterpart: this is a deployment
  * variant of the same computation.  The 2D-gradient scratch is a fixed array inside the library
- * (i4d_render_bwd_noalloc_max_records() records of 48 bytes, 24 MiB, held by every GPU that loads
+ * (i4d_render_bwd_noalloc_max_records() records of 36 bytes, 18 MiB, held by every GPU that loads
  * the library until exit) instead of the grad2d argument; all other arguments are as for
  * i4d_render_bwd.  Returns I4D_ERR_CAPACITY, launching nothing, when n_views * n exceeds the maximum.
  * Every call shares the array: calls that overlap on the GPU race.  Each call looks up the array's

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libi4d.so")
 
 MAX_VIEWS = 64
+GRAD2D_FLOATS = 9  # I4D_GRAD2D_FLOATS: floats per (view, Gaussian) record of the 2D-gradient scratch
 MODE_FULL, MODE_ISO_ROT, MODE_ISO_IDENTITY = 0, 1, 2
 LOSS_L1, LOSS_MSE = 0, 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "capacity exceeded", -3: "CUDA error", -4: "workspace too small"}

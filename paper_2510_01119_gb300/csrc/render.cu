@@ -467,11 +467,10 @@ __device__ __forceinline__ void phase_b(const BwdWarp& W, int half, int l16, int
 #pragma unroll
     for (int c = 0; c < 9; ++c) nz = nz || g[c] != 0.0f;
     if (nz) {
-      float* g0 = grad2d + (size_t)rr * 4;
-      float* g1 = g0 + VN * 4;
-      red_add4(g0, g[0], g[1], g[2], g[3]);
-      red_add4(g1, g[4], g[5], g[6], g[7]);
-      red_add(g1 + VN * 4, g[8]);
+      // planes: float4 (g0..g3), float4 (g4..g7), float (g8), each VN long
+      red_add4(grad2d + (size_t)rr * 4, g[0], g[1], g[2], g[3]);
+      red_add4(grad2d + (VN + rr) * 4, g[4], g[5], g[6], g[7]);
+      red_add(grad2d + VN * 8 + rr, g[8]);
     }
   }
 }

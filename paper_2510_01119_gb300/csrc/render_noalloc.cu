@@ -8,7 +8,7 @@
 // and stall the frame).  They still pass every input and output; only the scratch moves here.
 //
 // Costs and rules:
-//   - the array (kNoAllocMaxRecords x 3 float4 = 24 MiB) is held by every GPU that loads the library,
+//   - the array (kNoAllocMaxRecords x 9 floats = 18 MiB) is held by every GPU that loads the library,
 //     until the process exits;
 //   - every call shares it: calls that overlap on the GPU (different streams, or different host
 //     threads without ordering) race on it and corrupt each other's gradients;
@@ -29,7 +29,7 @@ namespace {
 constexpr int64_t kNoAllocMaxRecords = 1 << 19;  // n_views * n <= 524,288
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) float4 g_noalloc_grad2d[3 * kNoAllocMaxRecords];
+static __device__ __align__(256) float g_noalloc_grad2d[I4D_GRAD2D_FLOATS * kNoAllocMaxRecords];
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};

@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(128) slice_project_bwd_kernel(const float4* __
   for (int v = 0; v < vt.n_views; ++v) {
     const size_t r = (size_t)v * n + i;
     if (__ldg(&touched[r]) == 0) continue;
-    const float4 g0 = __ldg(&grad2d[r]), g1 = __ldg(&grad2d[VN + r]), g2 = __ldg(&grad2d[2 * VN + r]);
-    const float g[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+    const float4 g0 = __ldg(&grad2d[r]), g1 = __ldg(&grad2d[VN + r]);
+    const float g8 = __ldg(reinterpret_cast<const float*>(grad2d + 2 * VN) + r);
+    const float g[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g8};
     ViewFwd F;
     view_forward<DEG>(G, P + 5 * (size_t)n, n, i, sc[v], sx[v].campos, sx[v].tanx, sx[v].tany, S, F, nt);
     view_backward<DEG>(G, F, P + 5 * (size_t)n, n, i, sc[v], g, PG, gsh, gA, gc, gb, nt, gsch);

@@ -120,7 +120,7 @@ class Rasterizer:
         self.T_final = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
         self.last = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
         self.n_contrib = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
-        self.grad2d = torch.empty(3 * VN * 4, dtype=torch.float32, device=dev)
+        self.grad2d = torch.empty(L.GRAD2D_FLOATS * max(VN, 1), dtype=torch.float32, device=dev)
         self.grads = torch.empty(n_planes(self.sh_deg, self.sch_terms) * self.n * 4, dtype=torch.float32,
                                  device=dev)
         self._alloc_bins(capacity if capacity else max(1 << 16, 8 * VN))

@@ -29,6 +29,14 @@ def test_header_declares_the_boundary():
     assert len(names) >= 17
 
 
+def test_binding_constants_match_the_header():
+    from paper_2510_01119_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "i4d.h")).read()
+    const = {k: int(v) for k, v in re.findall(r"^#define (I4D_\w+) \(?(-?\d+)\)?", text, flags=re.M)}
+    assert const["I4D_MAX_VIEWS"] == _lib.MAX_VIEWS
+    assert const["I4D_GRAD2D_FLOATS"] == _lib.GRAD2D_FLOATS
+
+
 def test_every_declared_symbol_is_exported(lib):
     from paper_2510_01119_gb300 import _lib
     for name in declared_symbols():
