@@ -619,14 +619,17 @@ def run_ours(args, ws, rank, local):
     ms_max = max_over_ranks(ms, ws)
     overflow = step.overflowed()
 
-    # e2e through host buffers: H2D of the step's targets and cameras from pinned memory, D2H of the loss
-    pool = 4
+    # e2e through host buffers, on the same batches as the timed loop: the frames live in host memory;
+    # each step gathers its views' targets and cameras into a pinned staging buffer (a ring of three,
+    # each reused once the copy out of it has finished), copies them to the device, runs the step and
+    # copies the loss back
+    host_bank = {size: wl["bank"][size].cpu() for size in (FULL, HALF)}
+    host_cam_bank = {size: wl["cam_bank"][size].cpu() for size in (FULL, HALF)}
+    host_idx = [(torch.as_tensor(np.asarray(a, np.int64)), torch.as_tensor(np.asarray(b, np.int64))) for a, b in batches]
+    pool = 3
     host_tgt = [torch.empty(step.target.numel(), dtype=torch.float32).pin_memory() for _ in range(pool)]
     host_cam = [torch.empty(V, 20, dtype=torch.float32).pin_memory() for _ in range(pool)]
-    for j in range(pool):
-        load_batch(j)
-        host_tgt[j].copy_(step.target)
-        host_cam[j].copy_(step.cams)
+    copied = [None] * pool
     host_loss = torch.empty(args.steps, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     barrier(ws)
@@ -634,8 +637,19 @@ def run_ours(args, ws, rank, local):
     t_host0 = time.perf_counter()
     e0.record()
     for k in range(args.steps):
-        step.target.copy_(host_tgt[k % pool], non_blocking=True)
-        step.cams.copy_(host_cam[k % pool], non_blocking=True)
+        j = k % pool
+        if copied[j] is not None:
+            copied[j].synchronize()
+        fa, fb = host_idx[args.warmup + k]
+        ht = host_tgt[j]
+        torch.index_select(host_bank[FULL], 0, fa, out=ht[:N_FULL * fullpix].view(N_FULL, fullpix))
+        torch.index_select(host_bank[HALF], 0, fb, out=ht[N_FULL * fullpix:].view(N_HALF, halfpix))
+        torch.index_select(host_cam_bank[FULL], 0, fa, out=host_cam[j][:N_FULL])
+        torch.index_select(host_cam_bank[HALF], 0, fb, out=host_cam[j][N_FULL:])
+        step.target.copy_(ht, non_blocking=True)
+        step.cams.copy_(host_cam[j], non_blocking=True)
+        copied[j] = torch.cuda.Event()
+        copied[j].record()
         run()
         host_loss[k:k + 1].copy_(step.loss, non_blocking=True)
     e1.record()
