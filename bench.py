@@ -285,9 +285,11 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary of this kernel and workload, if it was
-    taken on the current kernel sources (else None)."""
+def stored_traffic(kernel: str, alg_bytes: float):
+    """DRAM bytes per launch of `kernel` on this run's batch: the committed ncu summary's measured
+    traffic for its captured batch, scaled by this batch's algorithmic bytes over the captured one's
+    (the traffic grows with the instances and records of a batch), if the summary was taken on the
+    current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_train_step_1M.md")
     if not os.path.exists(path):
         return None
@@ -299,9 +301,11 @@ def stored_traffic(kernel: str):
     if vals.get("source_hash") != source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        measured = float(vals["dram_bytes_per_launch"])
+        captured_alg = float(vals["algorithmic_bytes_per_launch"].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
+    return measured * alg_bytes / captured_alg
 
 
 def learned_init_summary():
@@ -600,6 +604,8 @@ def run_ours(args, ws, rank, local):
     for k in range(args.warmup):
         load_batch(k)
         run()
+    # the end-to-end loop below replays the same batches from the same training state
+    state0 = [t.clone() for t in (step.params, step.m, step.v, step.step_count)]
     torch.cuda.synchronize()
     barrier(ws)
     clocks = Clocks(local)
@@ -619,7 +625,8 @@ def run_ours(args, ws, rank, local):
     ms_max = max_over_ranks(ms, ws)
     overflow = step.overflowed()
 
-    # e2e through host buffers, on the same batches as the timed loop: the frames live in host memory;
+    # e2e through host buffers, on the same batches and from the same parameters and optimiser state as
+    # the timed loop (training makes later steps cheaper): the frames live in host memory;
     # each step gathers its views' targets and cameras into a pinned staging buffer (a ring of three,
     # each reused once the copy out of it has finished), copies them to the device, runs the step and
     # copies the loss back
@@ -631,6 +638,9 @@ def run_ours(args, ws, rank, local):
     host_cam = [torch.empty(V, 20, dtype=torch.float32).pin_memory() for _ in range(pool)]
     copied = [None] * pool
     host_loss = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+    for t, t0 in zip((step.params, step.m, step.v, step.step_count), state0):
+        t.copy_(t0)
+    del state0
     torch.cuda.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -689,7 +699,7 @@ def run_ours(args, ws, rank, local):
     alg = algorithmic_bytes(dominant, n, V, I, R_vis, P, passes)
     hbm_peak, peak_kind = measured_peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
-    traffic = stored_traffic(dominant)
+    traffic = stored_traffic(dominant, alg)
     hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
            "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic, "algorithmic_bytes": alg}
     if dominant in FLOPS_PER_BLENDED_PAIR:
