@@ -240,8 +240,8 @@ def algorithmic_bytes(kernel: str, n: int, V: int, I: int, R_vis: int, P: int, p
         return 4.0 * I + 36.0 * R_vis + 24.0 * P
     if kernel == "render_bwd":      # ids, records, 2D-grad atomics 36/visible record, inputs 20/pixel
         return 4.0 * I + 72.0 * R_vis + 20.0 * P
-    if kernel == "slice_project":   # 80 B params once, 52 B written per (view, Gaussian)
-        return 80.0 * n + 52.0 * V * n
+    if kernel == "slice_project":   # 80 B params once, the tile count per (view, Gaussian), a 64 B record per visible
+        return 80.0 * n + 4.0 * V * n + 64.0 * R_vis
     if kernel == "slice_project_bwd":  # params 80, touched 4/(view, Gaussian), 2D grads 36/visible, grads 80
         return 160.0 * n + 4.0 * V * n + 36.0 * R_vis
     if kernel == "radix_scatter":   # read key+value, write key+value

@@ -161,7 +161,8 @@ I4D_API int64_t i4d_param_floats_sch(int32_t sh_deg, int32_t sch_terms);
  *   g        host struct, params on the device
  *   views    host; cams: DEVICE array of views->n_views cameras
  *   settings host (NULL = defaults)
- *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 64-byte record layout
+ *   proj     DEVICE out, n_views * n * I4D_PROJ_FLOATS floats in the 64-byte record layout; a
+ *            record whose touched count is 0 is not written (its previous contents stay)
  *   touched  DEVICE out, n_views * n uint32: number of tiles of the record's rectangle
  *            (0 for culled or off-screen Gaussians)
  */

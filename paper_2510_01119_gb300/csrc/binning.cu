@@ -47,8 +47,7 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t x, uint64_t& excl) 
   return total;
 }
 
-// Element loaders of the scan: the value itself, 1 for a nonzero value, or a value gathered
-// through an index array.
+// Element loaders of the scan: the value itself, or 1 for a nonzero value.
 struct LoadPlain {
   const uint32_t* p;
   __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i]; }
@@ -56,11 +55,6 @@ struct LoadPlain {
 struct LoadNonzero {
   const uint32_t* p;
   __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i] != 0u ? 1u : 0u; }
-};
-struct LoadGather {
-  const uint32_t* idx;
-  const uint32_t* p;
-  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[idx[i]]; }
 };
 
 template <class Load>
@@ -272,11 +266,13 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restr
 // addresses (after the scanned histogram's offset for the block).
 // Compiled for 4 resident blocks per SM (at most 64 registers): the kernel waits on memory, and 32
 // warps hide more of it than 24 (0.60 against 0.69 ms per step with 8 keys per thread).
+// kgather (nullable): write kgather[value] in place of each key (the last pass of a sort whose
+// sorted keys are not needed but a per-value quantity is, in sorted order).
 template <class K>
 __global__ void __launch_bounds__(kRsThreads, 4) radix_scatter_kernel(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, const int64_t* __restrict__ n_dev, int64_t capacity, int shift, int nblocks,
-    const uint32_t* __restrict__ offs) {
+    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ kgather) {
   constexpr int kItems = RsCfg<K>::kItems, kTile = RsCfg<K>::kTile;
   __shared__ uint32_t cnt[kRsWarps][kRsBins];
   __shared__ uint32_t dstart[kRsBins];  // first slot of each digit in the block's digit-major layout
@@ -351,8 +347,9 @@ __global__ void __launch_bounds__(kRsThreads, 4) radix_scatter_kernel(
     const K k = skey[s];
     const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
     const uint32_t pos = gbase[d] + ((uint32_t)s - dstart[d]);
-    kout[pos] = k;
-    vout[pos] = sval[s];
+    const uint32_t v = sval[s];
+    kout[pos] = kgather ? (K)kgather[v] : k;
+    vout[pos] = v;
   }
 }
 
@@ -395,9 +392,10 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __rest
 // and share the records they gather in L2 (on the 1.13M-Gaussian, 8-view training batch the
 // backward's DRAM traffic falls from 2.26 to 1.80 GB against quarter-octave buckets, for 0.6% more
 // time in the two compositing kernels).  The order only decides which CTA starts first, never a
-// result.  One CTA of 1024 threads: a stable counting sort, ranked per warp with match_any and per
-// bucket by a scan over the warps.
-constexpr int kOrderBuckets = 33;  // octaves of lengths below 2^33
+// result.  One CTA of 32 warps: a stable counting sort over 32 buckets, each chunk of 1024 tiles
+// ranked per warp with match_any, and per bucket by warp k scanning bucket k's counts over the
+// warps.
+constexpr int kOrderBuckets = 32;  // octaves; lists of 2^31 entries or more share the first bucket
 
 __device__ __forceinline__ int order_bucket(uint32_t len) {
   return kOrderBuckets - 1 - min((int)floorf(log2f((float)len + 1.0f)), kOrderBuckets - 1);
@@ -406,44 +404,57 @@ __device__ __forceinline__ int order_bucket(uint32_t len) {
 __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __restrict__ ranges, int T,
                                                           uint32_t* __restrict__ order) {
   __shared__ uint32_t base[kOrderBuckets];
-  __shared__ uint32_t warp_pos[32][kOrderBuckets];
+  __shared__ uint32_t warp_pos[32][kOrderBuckets + 1];  // [warp][bucket], padded row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* wp = &warp_pos[0][0];
-  for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) base[k] = 0;
-  for (int k = threadIdx.x; k < 32 * kOrderBuckets; k += blockDim.x) wp[k] = 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  if (threadIdx.x < kOrderBuckets) base[threadIdx.x] = 0;
+  warp_pos[warp][lane] = 0;
   __syncthreads();
-  for (int t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&base[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+  // bucket sizes (warp-aggregated), then their exclusive scan by warp 0
+  for (int t0 = 0; t0 < T; t0 += blockDim.x) {
+    const int t = t0 + (int)threadIdx.x;
+    const int b = t < T ? order_bucket(ranges[2 * t + 1] - ranges[2 * t]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && (peers & lt_mask) == 0) atomicAdd(&base[b], (uint32_t)__popc(peers));
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int k = 0; k < kOrderBuckets; ++k) {
-      const uint32_t c = base[k];
-      base[k] = run;
-      run += c;
+  if (warp == 0) {
+    const uint32_t c = base[lane];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
+    base[lane] = incl - c;
   }
   __syncthreads();
   for (int t0 = 0; t0 < T; t0 += blockDim.x) {
     const int t = t0 + (int)threadIdx.x;
     const int b = t < T ? order_bucket(ranges[2 * t + 1] - ranges[2 * t]) : -1;
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const uint32_t rank = __popc(peers & lt_mask);
     if (b >= 0 && rank == 0) warp_pos[warp][b] = __popc(peers);
     __syncthreads();
-    // per bucket: warp counts -> positions (warps in index order), bucket base advanced by the chunk
-    for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) {
-      uint32_t run = base[k];
-      for (int w = 0; w < 32; ++w) {
-        const uint32_t c = warp_pos[w][k];
-        warp_pos[w][k] = run;
-        run += c;
+    {
+      // warp k: bucket k's counts over the warps (lane = warp index) -> each warp's first position
+      const int k = warp;
+      const uint32_t c = warp_pos[lane][k];
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      base[k] = run;
+      const uint32_t b0 = base[k];
+      warp_pos[lane][k] = b0 + incl - c;
+      __syncwarp();
+      if (lane == 31) base[k] = b0 + incl;
     }
     __syncthreads();
     if (b >= 0) order[warp_pos[warp][b] + rank] = (uint32_t)t;
     __syncthreads();
-    for (int k = threadIdx.x; k < 32 * kOrderBuckets; k += blockDim.x) wp[k] = 0;
+    warp_pos[warp][lane] = 0;
     __syncthreads();
   }
 }
@@ -485,10 +496,11 @@ size_t radix_workspace_bytes(int64_t capacity) {
 }
 
 // vals_out must be a buffer of its own (neither vals nor vals_alt): the last pass reads one of those.
+// key_gather (nullable): the last pass writes key_gather[value] in place of the sorted keys.
 template <class K>
 cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint32_t* vals_out,
                               int64_t capacity, const int64_t* n_dev, int bits, void* ws, K** keys_result,
-                              cudaStream_t st) {
+                              cudaStream_t st, const uint32_t* key_gather) {
   const int64_t nb64 = (capacity + RsCfg<K>::kTile - 1) / RsCfg<K>::kTile;
   const int nblocks = (int)(nb64 > 0 ? nb64 : 1);
   const int64_t hist_n = (int64_t)kRsBins * nblocks;
@@ -511,16 +523,18 @@ cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* va
     if (e != cudaSuccess) return e;
     I4D_PROF("radix_scatter", st);
     radix_scatter_kernel<K><<<nblocks, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, capacity, 8 * p, nblocks,
-                                                            hist);
+                                                            hist, p == passes - 1 ? key_gather : nullptr);
   }
   if (keys_result) *keys_result = kb[passes & 1];
   return cudaGetLastError();
 }
 
 template cudaError_t launch_radix_sort<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                 const int64_t*, int, void*, uint32_t**, cudaStream_t);
+                                                 const int64_t*, int, void*, uint32_t**, cudaStream_t,
+                                                 const uint32_t*);
 template cudaError_t launch_radix_sort<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, uint32_t*, int64_t,
-                                                 const int64_t*, int, void*, uint64_t**, cudaStream_t);
+                                                 const int64_t*, int, void*, uint64_t**, cudaStream_t,
+                                                 const uint32_t*);
 
 size_t bin_workspace_bytes(int64_t VN, int64_t capacity) {
   const size_t vn = (size_t)(VN > 0 ? VN : 1), cap = (size_t)(capacity > 0 ? capacity : 1);
@@ -567,12 +581,14 @@ cudaError_t launch_bin_tiles(const ViewTable& vt, int n, const float* proj_f, co
     I4D_PROF("visible_compact", st);
     visible_compact_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(VN, proj, touched, offs1, dkA, dvA);
   }
-  // 2. stable sort of the visible records by depth (equal depths keep index order)
-  e = launch_radix_sort<uint32_t>(dkA, dvA, dkB, dvB, dvOut, VN, R_dev, 32, radix_ws, nullptr, st);
+  // 2. stable sort of the visible records by depth (equal depths keep index order); the last pass
+  //    writes each record's tile count where its key would go
+  uint32_t* cnt_sorted = nullptr;
+  e = launch_radix_sort<uint32_t>(dkA, dvA, dkB, dvB, dvOut, VN, R_dev, 32, radix_ws, &cnt_sorted, st, touched);
   if (e != cudaSuccess) return e;
   uint32_t* rec_sorted = dvOut;
   // 3. tile counts in depth order -> output offsets; the total is the instance count
-  e = scan_impl(LoadGather{rec_sorted, touched}, offs2, VN, R_dev, n_inst, scan_ws, st);
+  e = scan_impl(LoadPlain{cnt_sorted}, offs2, VN, R_dev, n_inst, scan_ws, st);
   if (e != cudaSuccess) return e;
   if (VN > 0) {
     I4D_PROF("emit_keys", st);

@@ -19,12 +19,13 @@ size_t scan_workspace_bytes(int64_t n);
 cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int64_t* total, void* ws, cudaStream_t st);
 
 // stable LSD radix sort of (key, value) pairs on bits [0, bits), 8 bits per pass; the count is
-// min(*n_dev, capacity); the values of the last pass go to vals_out
+// min(*n_dev, capacity); the values of the last pass go to vals_out; with key_gather, the last pass
+// writes key_gather[value] in place of each sorted key
 size_t radix_workspace_bytes(int64_t capacity);
 template <class K>
 cudaError_t launch_radix_sort(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint32_t* vals_out,
                               int64_t capacity, const int64_t* n_dev, int bits, void* ws, K** keys_result,
-                              cudaStream_t st);
+                              cudaStream_t st, const uint32_t* key_gather = nullptr);
 
 // tile binning (visible records sorted by depth, pairs emitted in that order, stable sort by tile)
 size_t bin_workspace_bytes(int64_t VN, int64_t capacity);

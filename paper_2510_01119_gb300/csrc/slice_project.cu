@@ -3,7 +3,8 @@
 //
 // One thread per Gaussian loops over all views of the batch: the view-independent part (rotation,
 // 4D covariance, sigmoid) is computed once and the parameters are read from HBM once per launch,
-// not once per view.  Records are written as four float4 planes so every store is coalesced.
+// not once per view.  Each (view, Gaussian) record is one 64-byte record (four float4), written only
+// when the Gaussian covers a tile of the view.
 #include "gauss_math.cuh"
 #include "kernels.cuh"
 
@@ -60,15 +61,18 @@ __global__ void __launch_bounds__(256) slice_project_kernel(const float4* __rest
       cnt = (uint32_t)((x1 - x0) * (y1 - y0));
     }
     const size_t r = (size_t)v * n + i;
-    // the record as the compositing kernels stage it: conic scaled by kFalloff (exp(-q/2) =
-    // 2^(sa dx^2 + sb2 dx dy + sc dy^2)) and the exponent threshold of the kept test
-    // m >= kFalloff min(q_max, 2 ln(o_t / alpha_min)), computed once here instead of at every staging
-    const float m_thr = F.visible ? __fmul_rn(kFalloff, fminf(S.q_max, 2.0f * logf(F.ot / S.alpha_min))) : 0.0f;
-    float4* rec = proj + 4 * r;
-    rec[0] = box;
-    rec[1] = make_float4(F.u, F.v, __fmul_rn(kFalloff, F.conic[0]), __fmul_rn(2.0f * kFalloff, F.conic[1]));
-    rec[2] = make_float4(__fmul_rn(kFalloff, F.conic[2]), F.ot, m_thr, fmaxf(F.raw[0], 0.0f));
-    rec[3] = make_float4(fmaxf(F.raw[1], 0.0f), fmaxf(F.raw[2], 0.0f), F.m[2], F.radius);
+    if (cnt > 0) {
+      // the record as the compositing kernels stage it: conic scaled by kFalloff (exp(-q/2) =
+      // 2^(sa dx^2 + sb2 dx dy + sc dy^2)) and the exponent threshold of the kept test
+      // m >= kFalloff min(q_max, 2 ln(o_t / alpha_min)), computed once here instead of at every
+      // staging.  Records on no tile are never read, so they are not written.
+      const float m_thr = __fmul_rn(kFalloff, fminf(S.q_max, 2.0f * logf(F.ot / S.alpha_min)));
+      float4* rec = proj + 4 * r;
+      rec[0] = box;
+      rec[1] = make_float4(F.u, F.v, __fmul_rn(kFalloff, F.conic[0]), __fmul_rn(2.0f * kFalloff, F.conic[1]));
+      rec[2] = make_float4(__fmul_rn(kFalloff, F.conic[2]), F.ot, m_thr, fmaxf(F.raw[0], 0.0f));
+      rec[3] = make_float4(fmaxf(F.raw[1], 0.0f), fmaxf(F.raw[2], 0.0f), F.m[2], F.radius);
+    }
     touched[r] = cnt;
   }
 }

@@ -40,13 +40,15 @@ def test_sch_forward_and_backward_match_oracle(dev, orc, deg, nt):
     ov = oracle_views(orc, g, cams)
     bad, flagged, worst = compare_images([x.cpu().numpy() for x in rast.split_images()], ov)
     assert bad == 0, (bad, flagged, worst)
-    # records: the colour columns carry the SCH terms
+    # records: the colour columns carry the SCH terms (records on no tile are not written)
     n = g["mean4"].shape[0]
     rec = gpu_records(rast)
+    touched = rast.touched[:len(cams) * n].cpu().numpy()
     C = orc.P
     for v, cam in enumerate(cams):
         P = ov[v][0]
-        vis = P[:, C["visible"]] != 0
+        vis = (P[:, C["visible"]] != 0) & (touched[v * n:(v + 1) * n] > 0)
+        assert vis.sum() > 100
         got = np.c_[rec["r"], rec["g"], rec["b"]][v * n:(v + 1) * n]
         want = P[:, [C["r"], C["g"], C["b"]]]
         assert np.abs(got[vis] - want[vis]).max() < 2e-6
