@@ -527,7 +527,10 @@ def run_reference(args, ws, rank):
     sec = float(np.mean(est))
     value = 1.0 / sec
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": warmup, "steps_requested": args.steps, "ms_per_step": sec * 1e3,
+            "steps": steps, "warmup": warmup, "steps_requested": args.steps,
+            # what was timed: each step's bounded sample; the value is the whole 8-view step's rate,
+            # extrapolated from the sample
+            "ms_per_step": float(np.mean(wall)) * 1e3, "ms_per_step_full_workload": sec * 1e3,
             "extrapolated": True, "sample_wall_s_per_step": float(np.mean(wall)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "train_step_1M_8views", "n_gaussians": int(g["mean4"].shape[0]),
